@@ -1,0 +1,248 @@
+"""FP64 CPU oracle for AIR (arXiv 1310.1434) -- TEST INFRASTRUCTURE ONLY.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It is a plain, slow, double-precision
+C implementation (``oracle/*.c``, built with gcc) of what the GPU library
+computes, written from the paper's definitions and sharing no code with it:
+
+* ``project`` / ``backproject``: the X-ray transform A of Eq. (1) by Siddon's
+  method and its explicit transpose;
+* ``filter`` / ``filtered_backproject``: the filtration C of Eq. (2) (FFT
+  Ram-Lak, linear convolution) and A'^T = A^T C of Eq. (5);
+* ``framelet`` / ``framelet_adjoint`` / ``shrink``: the tensor framelet W and
+  the split-Bregman d/b update;
+* ``cg`` / ``solve``: the CG-solved L2 step and the split-Bregman loop.
+
+Pins against the paper and the mathematics live in ``tests/test_oracle_*.py``.
+Parity of the full-size configurations beyond those pins is "parity
+unpinned": the oracle is then the reference by construction.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = ["siddon.c", "ramp.c", "framelet.c", "solver.c"]
+_LIB_PATH = os.path.join(_HERE, "_build", "liborc.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP, no fast-math) into _build/."""
+    srcs = [os.path.join(_HERE, s) for s in _SRC] + [os.path.join(_HERE, "orc.h")]
+    if not force and os.path.exists(_LIB_PATH):
+        t = os.path.getmtime(_LIB_PATH)
+        if all(os.path.getmtime(s) <= t for s in srcs):
+            return _LIB_PATH
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
+           "-fopenmp", "-fno-fast-math", "-ffp-contract=off", "-o", tmp] + \
+          [os.path.join(_HERE, s) for s in _SRC] + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Geom(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("pixel_mm", ctypes.c_double),
+                ("n_views", ctypes.c_int), ("n_bins", ctypes.c_int),
+                ("dso_mm", ctypes.c_double), ("dsd_mm", ctypes.c_double),
+                ("dgamma", ctypes.c_double), ("beta0", ctypes.c_double),
+                ("arc", ctypes.c_double), ("filter", ctypes.c_int)]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.POINTER
+        d = ctypes.c_double
+        g = P(_Geom)
+        dp = P(d)
+        sig = {
+            "orc_dgamma": (d, [g]),
+            "orc_ray": (None, [g, ctypes.c_int, ctypes.c_int, dp, dp]),
+            "orc_ray_segments": (ctypes.c_int, [g, ctypes.c_int, ctypes.c_int,
+                                                P(ctypes.c_int), dp, ctypes.c_int]),
+            "orc_project_ray": (d, [g, dp, ctypes.c_int, ctypes.c_int]),
+            "orc_project": (None, [g, dp, dp]),
+            "orc_backproject": (None, [g, dp, dp]),
+            "orc_ramp_tap": (d, [ctypes.c_int]),
+            "orc_ramp_scale": (d, [g]),
+            "orc_filter": (None, [g, dp, dp]),
+            "orc_filtered_backproject": (None, [g, dp, dp]),
+            "orc_framelet": (None, [ctypes.c_int, dp, dp]),
+            "orc_framelet_adjoint": (None, [ctypes.c_int, dp, dp]),
+            "orc_soft": (d, [d, d]),
+            "orc_shrink": (d, [ctypes.c_int, dp, dp, dp, d]),
+            "orc_cg": (None, [g, dp, d, ctypes.c_int, dp]),
+            "orc_solve": (None, [g, dp, d, d, ctypes.c_int, ctypes.c_int, dp, dp]),
+            "orc_threads": (ctypes.c_int, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+@dataclass
+class Geometry:
+    """Fan-beam geometry (mm, rad); mirrors the fields of the C struct."""
+    n: int
+    pixel_mm: float
+    n_views: int
+    n_bins: int
+    dso_mm: float = 850.0
+    dsd_mm: float = 1450.0
+    dgamma: float = 0.0
+    beta0: float = 0.0
+    arc: float = 2.0 * np.pi
+    filter: int = 1
+
+    def _c(self) -> _Geom:
+        return _Geom(self.n, self.pixel_mm, self.n_views, self.n_bins, self.dso_mm,
+                     self.dsd_mm, self.dgamma, self.beta0, self.arc, self.filter)
+
+
+def _geom(g) -> _Geom:
+    if isinstance(g, _Geom):
+        return g
+    if isinstance(g, Geometry):
+        return g._c()
+    return Geometry(**{k: getattr(g, k) for k in Geometry.__dataclass_fields__})._c()
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def threads() -> int:
+    return _load().orc_threads()
+
+
+def dgamma(g) -> float:
+    return _load().orc_dgamma(ctypes.byref(_geom(g)))
+
+
+def ray(g, v: int, j: int):
+    s = np.zeros(2)
+    u = np.zeros(2)
+    _load().orc_ray(ctypes.byref(_geom(g)), v, j, _dptr(s), _dptr(u))
+    return s, u
+
+
+def ray_segments(g, v: int, j: int):
+    """(pixel indices, lengths) of ray (v, j), in the order Siddon visits them."""
+    cg = _geom(g)
+    cap = 4 * cg.n + 8
+    pix = np.zeros(cap, dtype=np.int32)
+    ln = np.zeros(cap)
+    m = _load().orc_ray_segments(ctypes.byref(cg), v, j,
+                                 pix.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dptr(ln), cap)
+    return pix[:m].copy(), ln[:m].copy()
+
+
+def project_ray(g, X, v: int, j: int) -> float:
+    X = _f64(X)
+    return _load().orc_project_ray(ctypes.byref(_geom(g)), _dptr(X), v, j)
+
+
+def project(g, X) -> np.ndarray:
+    cg = _geom(g)
+    X = _f64(X).reshape(-1)
+    assert X.size == cg.n * cg.n
+    Y = np.zeros((cg.n_views, cg.n_bins))
+    _load().orc_project(ctypes.byref(cg), _dptr(X), _dptr(Y))
+    return Y
+
+
+def backproject(g, Y) -> np.ndarray:
+    cg = _geom(g)
+    Y = _f64(Y).reshape(-1)
+    assert Y.size == cg.n_views * cg.n_bins
+    X = np.zeros((cg.n, cg.n))
+    _load().orc_backproject(ctypes.byref(cg), _dptr(Y), _dptr(X))
+    return X
+
+
+def ramp_tap(k: int) -> float:
+    return _load().orc_ramp_tap(k)
+
+
+def ramp_scale(g) -> float:
+    return _load().orc_ramp_scale(ctypes.byref(_geom(g)))
+
+
+def filter(g, Y) -> np.ndarray:  # noqa: A001 - the paper's name for C
+    cg = _geom(g)
+    Y = _f64(Y).reshape(-1)
+    Z = np.zeros((cg.n_views, cg.n_bins))
+    _load().orc_filter(ctypes.byref(cg), _dptr(Y), _dptr(Z))
+    return Z
+
+
+def filtered_backproject(g, Y) -> np.ndarray:
+    cg = _geom(g)
+    Y = _f64(Y).reshape(-1)
+    X = np.zeros((cg.n, cg.n))
+    _load().orc_filtered_backproject(ctypes.byref(cg), _dptr(Y), _dptr(X))
+    return X
+
+
+def framelet(X) -> np.ndarray:
+    X = _f64(X)
+    n = X.shape[0]
+    c = np.zeros((9, n, n))
+    _load().orc_framelet(n, _dptr(X), _dptr(c))
+    return c
+
+
+def framelet_adjoint(c) -> np.ndarray:
+    c = _f64(c)
+    n = c.shape[1]
+    X = np.zeros((n, n))
+    _load().orc_framelet_adjoint(n, _dptr(c), _dptr(X))
+    return X
+
+
+def soft(t: float, tau: float) -> float:
+    return _load().orc_soft(t, tau)
+
+
+def shrink(X, b, tau: float):
+    """Returns (b_new, g, ||WX - d||_2); b is not modified."""
+    X = _f64(X)
+    n = X.shape[0]
+    bn = _f64(b).copy()
+    g = np.zeros((n, n))
+    r = _load().orc_shrink(n, _dptr(X), _dptr(bn), _dptr(g), tau)
+    return bn, g, r
+
+
+def cg(g, rhs, mu: float, n_cg: int, X0=None) -> np.ndarray:
+    cg_ = _geom(g)
+    rhs = _f64(rhs)
+    X = np.zeros((cg_.n, cg_.n)) if X0 is None else _f64(X0).copy()
+    _load().orc_cg(ctypes.byref(cg_), _dptr(rhs), mu, n_cg, _dptr(X))
+    return X
+
+
+def solve(g, Y, lam: float, mu: float, n_outer: int, n_cg: int, return_resid=False):
+    cg_ = _geom(g)
+    Y = _f64(Y)
+    X = np.zeros((cg_.n, cg_.n))
+    r = np.zeros(max(n_outer, 1))
+    _load().orc_solve(ctypes.byref(cg_), _dptr(Y), lam, mu, n_outer, n_cg, _dptr(X), _dptr(r))
+    return (X, r[:n_outer]) if return_resid else X

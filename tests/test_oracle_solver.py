@@ -1,0 +1,114 @@
+"""Pins of the oracle's CG and split-Bregman solver on tiny problems, against
+dense linear algebra and an independent primal-dual (Chambolle-Pock) solve of
+the same objective 1/2 ||P(AX - Y)||^2 + lambda ||W_hp X||_1 (Eqs. 1-5)."""
+import numpy as np
+import pytest
+
+import oracle
+from dense import dense_A, dense_C, dense_W
+
+N8 = 8
+V8, B8 = 32, 32   # enough views and bins that A'^T A is well conditioned
+
+
+def small_geom(filter_=1):
+    return oracle.Geometry(n=N8, pixel_mm=1.25, n_views=V8, n_bins=B8, filter=filter_)
+
+
+@pytest.fixture(scope="module")
+def mats():
+    g = small_geom()
+    A = dense_A(g)
+    return {1: (A, dense_C(g)), 0: (A, dense_C(small_geom(0)))}
+
+
+def smooth_truth():
+    y, x = np.mgrid[0:N8, 0:N8] / (N8 - 1.0)
+    X = 0.02 * (np.exp(-((x - 0.4) ** 2 + (y - 0.6) ** 2) / 0.08) + (x > 0.7))
+    return X
+
+
+def test_dense_C_matches_oracle_filter(mats):
+    g = small_geom()
+    _, C = mats[1]
+    Y = np.random.Generator(np.random.PCG64(1)).random((V8, B8))
+    assert np.allclose(oracle.filter(g, Y).ravel(), C @ Y.ravel(), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("filt", [1, 0])
+def test_cg_matches_dense_solve(mats, filt):
+    g = small_geom(filt)
+    A, C = mats[filt]
+    mu = 0.05 if filt else 2.0
+    M = A.T @ C @ A + mu * np.eye(N8 * N8)
+    rhs = np.random.Generator(np.random.PCG64(2)).standard_normal(N8 * N8)
+    ref = np.linalg.solve(M, rhs)
+    X = oracle.cg(g, rhs.reshape(N8, N8), mu, 64)
+    assert np.linalg.norm(X.ravel() - ref) <= 1e-8 * np.linalg.norm(ref)
+    # warm start: more steps from the answer keep the answer
+    X2 = oracle.cg(g, rhs.reshape(N8, N8), mu, 5, X0=ref.reshape(N8, N8))
+    assert np.linalg.norm(X2.ravel() - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+def test_cg_stops_on_zero_residual():
+    g = small_geom()
+    X = oracle.cg(g, np.zeros((N8, N8)), 1.0, 10)
+    assert np.all(X == 0.0)
+
+
+def test_split_bregman_small_lambda_gives_least_squares(mats):
+    # lambda -> 0: no shrinkage, so the outer loop is a proximal-point
+    # iteration converging to min ||P(AX - Y)||, i.e. A^T C A X = A^T C Y.
+    g = small_geom()
+    A, C = mats[1]
+    Y = (A @ smooth_truth().ravel()).reshape(V8, B8)
+    Y += 1e-3 * np.random.Generator(np.random.PCG64(3)).standard_normal(Y.shape)
+    ref = np.linalg.solve(A.T @ C @ A, A.T @ C @ Y.ravel())
+    X = oracle.solve(g, Y, 0.0, 0.05, 60, 64)
+    assert np.linalg.norm(X.ravel() - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+def objective(A, C, W, X, Y, lam):
+    r = A @ X - Y
+    return 0.5 * r @ C @ r + lam * np.abs((W @ X)[N8 * N8:]).sum()
+
+
+def chambolle_pock(A, C, W, Y, lam, iters=30000):
+    """PDHG on min_X G(X) + F(K X), K = high-pass framelet bands (||K|| <= 1),
+    G = 1/2 (AX-Y)^T C (AX-Y) (prox by a dense solve), F = lam ||.||_1."""
+    K = W[N8 * N8:]
+    n = A.shape[1]
+    tau = sigma = 0.99
+    H = A.T @ C @ A
+    Pinv = np.linalg.inv(np.eye(n) + tau * H)
+    c = tau * (A.T @ C @ Y)
+    x = np.zeros(n)
+    xb = x.copy()
+    z = np.zeros(K.shape[0])
+    for _ in range(iters):
+        z = np.clip(z + sigma * (K @ xb), -lam, lam)
+        xn = Pinv @ (x - tau * (K.T @ z) + c)
+        xb = 2 * xn - x
+        x = xn
+    return x
+
+
+@pytest.mark.parametrize("filt", [1, 0])
+def test_split_bregman_matches_primal_dual(mats, filt):
+    # (filt = 0 is TF-regularised IR, the same solver with C = I)
+    g = small_geom(filt)
+    A, C = mats[filt]
+    W = dense_W(N8)
+    Y = A @ smooth_truth().ravel()
+    Y += 2e-3 * np.random.Generator(np.random.PCG64(4)).standard_normal(Y.shape)
+    lam = 2e-4 if filt else 4e-3
+    mu = 2.0 if filt else 30.0      # ADMM penalty near the spectrum of A'^T A
+    X, resid = oracle.solve(g, Y.reshape(V8, B8), lam, mu, 1000, 30, return_resid=True)
+    Xcp = chambolle_pock(A, C, W, Y, lam)
+    f_sb = objective(A, C, W, X.ravel(), Y, lam)
+    f_cp = objective(A, C, W, Xcp, Y, lam)
+    assert abs(f_sb - f_cp) <= 1e-8 * abs(f_cp)
+    # the shrinkage is active (the L1 term matters) ...
+    assert np.count_nonzero(np.abs((W @ Xcp)[N8 * N8:]) < 1e-9) > 5
+    # ... and the split constraint d = W X is met in the limit
+    assert resid[-1] <= 1e-6 * max(resid[0], 1e-30) + 1e-12
