@@ -1,0 +1,172 @@
+// Internal types and device helpers of the AIR library (sm_103a).
+//
+// Every operator of the hot path is written as a TILE function: one thread
+// block of AIR_THREADS threads does one tile of one slice.  The same tile
+// functions back three launch forms:
+//   * per-op kernels over one slice            (air_project, air_solve, ...)
+//   * a task-table kernel over many slices      (serving: mixed ops per step)
+//   * a persistent kernel with a bounded grid barrier between phases
+//     (air_solve_batch)
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/air.h"
+
+#define AIR_THREADS 256
+
+namespace air { constexpr int RAMP_MAX_BINS = 8192; }  // largest n_bins (filter row in shared memory)
+
+namespace air {
+
+// ---------------------------------------------------------------- ops ----
+enum Op : int {
+    OP_NOP = 0,
+    OP_FWD,        // z = A src                      (src = x or p)
+    OP_RAMP,       // zc = C src                     (src = y or z), FP32
+    OP_RAMP_TC,    // zc = C z on tensor cores (split BF16) -- own kernel
+    OP_BWD,        // A^T zc with a mode epilogue (see BwdMode)
+    OP_CG_A,       // alpha; x += alpha p; r -= alpha q; rho' = r.r
+    OP_CG_B,       // p = r + beta p
+    OP_SHRINK,     // t = Wx + b; b' = t - d; g = W^T(d - b'); ||Wx - d||
+    OP_ZERO,       // x = 0, b = 0, g = 0, cg.stop = 0
+    OP_FRAMELET,   // out = W in            (API call)
+    OP_FRAMELET_T, // out = W^T in          (API call)
+    OP_TRANSPOSE,  // xt = transpose(src)   (before every OP_FWD; arg = FwdSrc)
+    OP_COUNT
+};
+
+enum FwdSrc : int { SRC_X = 0, SRC_P = 1, SRC_EXT = 2 };
+enum RampSrc : int { RSRC_Y = 0, RSRC_Z = 1, RSRC_EXT = 2 };
+enum BwdMode : int {
+    BWD_PLAIN = 0,   // out = dx * acc                      (air_backproject)
+    BWD_RHS0 = 1,    // rhs0 = dx * acc
+    BWD_RESID = 2,   // r = rhs0 + mu g - (dx acc + mu x); p = r; rho = r.r
+    BWD_Q = 3        // q = dx acc + mu p; pq = p.q; stop if pq <= 0
+};
+
+// Device-resident CG / Bregman scalars of one slice.  FP64 where the paper's
+// inner products and residual norms are formed.
+struct CgState {
+    double rho;        // r.r of the current CG iterate
+    double pq;         // p.Mp
+    double alpha, beta;
+    double resid;      // ||W X - d||_2 of the last shrink
+    int stop;          // CG of this outer step has stopped (rho == 0 or pq <= 0)
+    int outer;         // outer iterations done (indexes the resid output)
+    unsigned counter;  // blocks done in the current reducing phase
+    int pad;
+};
+
+// One ray in fixed point (32 fractional bits, pixel units, origin at the
+// image corner).  A ray with |ux| >= |uy| (o = 1) is walked column by column:
+// in column k its y-span is [lo(k), lo(k) + Ma] with lo(k) = L0 + k*M; a ray
+// with |uy| > |ux| (o = 0) is walked row by row with x and y exchanged.  The
+// length inside pixel (k, row) is ov * c, ov the integer overlap of the span
+// with [row, row + 1), c = sec/|M|.  Integer arithmetic is exact, so every
+// kernel that evaluates a (ray, pixel) pair gets the same length, bit for bit.
+struct __align__(16) RayFx {
+    long long L0;      // lower edge of the span in column (row) 0, 2^-32 px
+    long long M;       // slope * 2^32; 0 < |M| <= 2^32 - 1
+    float c;           // sec / |M|: length (px) per unit of overlap
+    unsigned Ma;       // |M|
+    int kk;            // walk range [kk & 0xffff, kk >> 16)
+    int o;             // 1: walk columns (reads X^T), 0: walk rows (reads X)
+};
+
+// Everything a tile function needs to know about one slice.  Plain data:
+// copied by value into kernel parameters or into a device task table.
+struct SliceDesc {
+    // geometry (pixel units: lengths divided by dx, image centre at 0)
+    int n, V, nb;
+    float half_n;        // n / 2
+    float dx;            // mm per pixel
+    float inv_dgamma;    // 1 / bin pitch
+    float jmid;          // (nb - 1) / 2
+    float half_k;        // bound factor of the backprojector's bin search (see bwd_pixel)
+    int filter;          // AIR_FILTER_*
+    // tables (plan-owned, read-only)
+    const RayFx *ray;    // [V*nb] fixed-point rays
+    const float4 *view;  // [V] {sx, sy, cx, cy}: source, unit central-ray direction
+    const float *taps;   // [nb] c0 * h[k], k = 0..nb-1 (h even)
+    float ramp_diag;     // taps[0] + 2 sum_{odd m < nb} taps[m]
+    // solver state (plan-owned workspace)
+    float *x, *r, *p, *q, *rhs0, *g;   // n*n
+    float *xt;                         // n*n: transposed copy of the projector's input
+    float *b, *b2;                     // 9*n*n each (Bregman variable, double-buffered)
+    float *z, *zc;                     // V*nb
+    const float *y;                    // V*nb measured sinogram
+    float mu, tau;                     // mu, lambda/mu
+    CgState *cg;
+    double *partial;                   // per-tile partial sums (>= max reducing tiles)
+    double *resid_out;                 // n_outer doubles or nullptr
+    // operands of the stand-alone API calls
+    const float *ext_in;
+    float *ext_out;
+    float *ext_out2;
+    double *ext_scalar;
+};
+
+struct Task {
+    int slice;      // index into the SliceDesc table
+    int op;         // Op
+    int arg;        // FwdSrc / RampSrc / BwdMode
+    int tile0;      // first global tile (block) index of this task
+};
+
+// ---------------------------------------------------- tile counts --------
+__host__ __device__ inline int tiles_fwd(const SliceDesc &s) {
+    return (s.V * s.nb + AIR_THREADS - 1) / AIR_THREADS;
+}
+__host__ __device__ inline int tiles_ramp(const SliceDesc &s) { return s.V; }
+// backprojector tile: 8 x 8 pixels, the views split over 4 interleaved groups
+constexpr int BWD_TX = 8, BWD_TY = 8, BWD_GROUPS = AIR_THREADS / (BWD_TX * BWD_TY);
+__host__ __device__ inline int tiles_bwd(const SliceDesc &s) {
+    return ((s.n + BWD_TX - 1) / BWD_TX) * ((s.n + BWD_TY - 1) / BWD_TY);
+}
+constexpr int VEC_PER_TILE = AIR_THREADS * 4;   // elementwise ops: 4 per thread
+__host__ __device__ inline int tiles_vec(const SliceDesc &s) {
+    return (s.n * s.n + VEC_PER_TILE - 1) / VEC_PER_TILE;
+}
+constexpr int SHR_T = 32;                      // shrink/framelet output tile
+__host__ __device__ inline int tiles_shr(const SliceDesc &s) {
+    return ((s.n + SHR_T - 1) / SHR_T) * ((s.n + SHR_T - 1) / SHR_T);
+}
+__host__ __device__ inline int tiles_of(const SliceDesc &s, int op) {
+    switch (op) {
+    case OP_FWD: return tiles_fwd(s);
+    case OP_RAMP: return tiles_ramp(s);
+    case OP_BWD: return tiles_bwd(s);
+    case OP_CG_A: case OP_CG_B: case OP_ZERO: return tiles_vec(s);
+    case OP_SHRINK: case OP_FRAMELET: case OP_FRAMELET_T: case OP_TRANSPOSE: return tiles_shr(s);
+    default: return 0;
+    }
+}
+// largest number of tiles of any reducing op: sizes SliceDesc::partial
+__host__ inline int max_reduce_tiles(const SliceDesc &s) {
+    int a = tiles_bwd(s), b = tiles_vec(s), c = tiles_shr(s);
+    return a > b ? (a > c ? a : c) : (b > c ? b : c);
+}
+
+// ------------------------------------------------ block reductions -------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+// Sum over the block, result valid in thread 0.  Fixed order: deterministic.
+__device__ __forceinline__ double block_sum(double v, double *sh /* >= 8 */) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < (AIR_THREADS >> 5); ++i) t += sh[i];
+    }
+    return t;
+}
+
+}  // namespace air

@@ -1,0 +1,479 @@
+// Host side of the AIR library: plans (geometry tables + workspace), argument
+// checking, the stand-alone operator calls and the solver programs.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "host_common.h"
+#include "launch.h"
+#include "ramp_tc.h"
+
+using namespace air;
+
+namespace air {
+
+thread_local std::string g_err;
+
+air_status fail(air_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+double fan_pitch(const air_geometry &g) {
+    if (g.dgamma > 0.0) return g.dgamma;
+    return 2.0 * std::asin(g.n * g.pixel_mm / std::sqrt(2.0) / g.dso_mm) / g.n_bins;
+}
+
+air_status validate_geometry(const air_geometry *g) {
+    if (!g) return fail(AIR_ERR_INVALID_ARG, "geometry is NULL");
+    if (g->n < 1 || g->n > 4096) return fail(AIR_ERR_INVALID_ARG, "n must be in 1..4096");
+    if (!(g->pixel_mm > 0.0) || !std::isfinite(g->pixel_mm))
+        return fail(AIR_ERR_INVALID_ARG, "pixel_mm must be > 0");
+    if (g->n_views < 1 || g->n_views > 65536) return fail(AIR_ERR_INVALID_ARG, "n_views must be in 1..65536");
+    if (g->n_bins < 1 || g->n_bins > RAMP_MAX_BINS) return fail(AIR_ERR_INVALID_ARG, "n_bins must be in 1..8192");
+    if ((long long)g->n_views * g->n_bins > (1ll << 26))
+        return fail(AIR_ERR_INVALID_ARG, "n_views * n_bins must be <= 2^26");
+    const double rc = g->n * g->pixel_mm / std::sqrt(2.0);
+    if (!(g->dso_mm >= rc + 8.0 * g->pixel_mm) || !std::isfinite(g->dso_mm))
+        return fail(AIR_ERR_INVALID_ARG,
+                    "dso_mm must exceed the image's circumscribed radius n*dx/sqrt(2) by 8 pixels");
+    if (!(g->dgamma >= 0.0) || !std::isfinite(g->dgamma)) return fail(AIR_ERR_INVALID_ARG, "dgamma must be >= 0");
+    if (!std::isfinite(g->beta0) || !std::isfinite(g->arc) || g->arc == 0.0)
+        return fail(AIR_ERR_INVALID_ARG, "beta0 must be finite and arc finite and nonzero");
+    if (g->filter != AIR_FILTER_NONE && g->filter != AIR_FILTER_RAMLAK)
+        return fail(AIR_ERR_INVALID_ARG, "filter must be AIR_FILTER_NONE or AIR_FILTER_RAMLAK");
+    if (g->precision != AIR_PREC_FP32 && g->precision != AIR_PREC_BF16X3)
+        return fail(AIR_ERR_INVALID_ARG, "precision must be AIR_PREC_FP32 or AIR_PREC_BF16X3");
+    return AIR_OK;
+}
+
+// Device pointer check: non-NULL, 16-byte aligned, and device accessible
+// (a host pointer handed to a kernel would fault the GPU).
+air_status check_dev_ptr(const void *p, const char *what) {
+    if (!p) return fail(AIR_ERR_INVALID_ARG, std::string(what) + " is NULL");
+    if (reinterpret_cast<uintptr_t>(p) & 15u)
+        return fail(AIR_ERR_INVALID_ARG, std::string(what) + " is not 16-byte aligned");
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(AIR_ERR_INVALID_ARG, std::string(what) + " is not a CUDA pointer");
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return fail(AIR_ERR_INVALID_ARG, std::string(what) + " is not device memory");
+    return AIR_OK;
+}
+
+bool overlap(const void *a, size_t na, const void *b, size_t nb) {
+    const char *pa = (const char *)a, *pb = (const char *)b;
+    return pa < pb + nb && pb < pa + na;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace air
+
+// -------------------------------------------------------------------- plan
+namespace {
+long long floor_div(long long a, long long b) {   // b > 0
+    long long q = a / b;
+    return (a % b != 0 && a < 0) ? q - 1 : q;
+}
+long long ceil_div(long long a, long long b) {    // b > 0
+    return -floor_div(-a, b);
+}
+}  // namespace
+
+// The fixed-point form of the line through (px, py) with unit direction
+// (ux, uy), pixel units with the origin at the image corner (see RayFx).
+RayFx air::make_ray_fx(double px, double py, double ux, double uy, int n) {
+    const double two32 = 4294967296.0;
+    const bool cols = std::fabs(ux) >= std::fabs(uy);       // walk columns
+    const double a = cols ? px : py, b = cols ? py : px;    // along / across the walk
+    const double ua = cols ? ux : uy, ub = cols ? uy : ux;
+    const double m = ub / ua;                               // |m| <= 1
+    const double y0 = b - a * m;                            // across-coordinate at walk-coordinate 0
+    long long M = std::llround(m * two32);
+    const long long mmax = (1ll << 32) - 1;
+    if (M > mmax) M = mmax;
+    if (M < -mmax) M = -mmax;
+    if (M == 0) M = 1;        // an exactly axis-parallel ray, tilted by 2^-32
+    const long long Y0 = std::llround(y0 * two32);
+    RayFx r{};
+    r.M = M;
+    r.L0 = Y0 + (M < 0 ? M : 0);
+    r.Ma = (unsigned)(M < 0 ? -M : M);
+    r.c = (float)((1.0 / std::fabs(ua)) / (double)r.Ma);
+    r.o = cols ? 1 : 0;
+    // walk range: columns k in [0, n) whose span [lo, lo + Ma] meets rows [0, n)
+    const long long N2 = (long long)n << 32;
+    long long ks, ke;
+    if (M > 0) {
+        ks = floor_div(-r.L0 - (long long)r.Ma, M) + 1;     // hi(k) > 0
+        ke = ceil_div(N2 - r.L0, M);                        // lo(k) < N2
+    } else {
+        const long long Mp = -M;
+        ks = floor_div(r.L0 - N2, Mp) + 1;                  // lo(k) < N2
+        ke = ceil_div(r.L0 + (long long)r.Ma, Mp);          // hi(k) > 0
+    }
+    if (ks < 0) ks = 0;
+    if (ke > n) ke = n;
+    if (ke < ks) ke = ks;
+    auto meets = [&](long long k) {
+        const long long lo = r.L0 + k * M;
+        return lo + (long long)r.Ma > 0 && lo < N2;
+    };
+    while (ks < ke && !meets(ks)) ++ks;
+    while (ke > ks && !meets(ke - 1)) --ke;
+    r.kk = (int)(ks | (ke << 16));
+    return r;
+}
+
+air_status plan_build(const air_geometry *geom, air_plan *P) {
+    const air_geometry &g = *geom;
+    const int n = g.n, V = g.n_views, nb = g.n_bins;
+    const size_t nn = (size_t)n * n, rays = (size_t)V * nb;
+    SliceDesc s{};
+    s.n = n;
+    s.V = V;
+    s.nb = nb;
+    s.half_n = 0.5f * n;
+    s.dx = (float)g.pixel_mm;
+    const double dg = fan_pitch(g);
+    s.inv_dgamma = (float)(1.0 / dg);
+    s.jmid = 0.5f * (nb - 1);
+    s.filter = g.filter;
+
+    // carve one allocation
+    struct Piece { void **dst; size_t bytes; };
+    float *x, *r, *p, *q, *rhs0, *gg, *b, *b2, *z, *zc, *ybuf, *xbuf, *xt;
+    RayFx *ray;
+    float4 *view;
+    float *taps;
+    CgState *cg;
+    double *partial;
+    const size_t npart = (size_t)max_reduce_tiles(s) + 64;
+    std::vector<Piece> pieces = {
+        {(void **)&ray, rays * sizeof(RayFx)}, {(void **)&view, (size_t)V * sizeof(float4)},
+        {(void **)&xt, nn * 4},
+        {(void **)&taps, (size_t)nb * sizeof(float)},
+        {(void **)&x, nn * 4}, {(void **)&r, nn * 4}, {(void **)&p, nn * 4}, {(void **)&q, nn * 4},
+        {(void **)&rhs0, nn * 4}, {(void **)&gg, nn * 4}, {(void **)&b, 9 * nn * 4}, {(void **)&b2, 9 * nn * 4},
+        {(void **)&z, rays * 4}, {(void **)&zc, rays * 4}, {(void **)&ybuf, rays * 4}, {(void **)&xbuf, nn * 4},
+        {(void **)&cg, sizeof(CgState)}, {(void **)&partial, npart * sizeof(double)}};
+    size_t total = 0;
+    for (auto &pc : pieces) total = align_up(total, 256) + pc.bytes;
+    total = align_up(total, 256);
+    char *mem = nullptr;
+    if (cudaMalloc(&mem, total) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(AIR_ERR_OOM, "cudaMalloc of the plan workspace failed (" + std::to_string(total) + " bytes)");
+    }
+    size_t off = 0;
+    for (auto &pc : pieces) {
+        off = align_up(off, 256);
+        *pc.dst = mem + off;
+        off += pc.bytes;
+    }
+
+    // geometry tables, computed in FP64: per view the source (pixel units,
+    // centred) and the central-ray direction; per ray the fixed-point line
+    std::vector<RayFx> hray(rays);
+    std::vector<float4> hview(V);
+    std::vector<float> htaps(nb);
+    const double inv_dx = 1.0 / g.pixel_mm;
+    for (int v = 0; v < V; ++v) {
+        const double beta = g.beta0 + g.arc * (double)v / (double)V;
+        const double cb = std::cos(beta), sb = std::sin(beta);
+        const double Sx = g.dso_mm * cb, Sy = g.dso_mm * sb;
+        hview[v] = make_float4((float)(Sx * inv_dx), (float)(Sy * inv_dx), (float)(-cb), (float)(-sb));
+        for (int j = 0; j < nb; ++j) {
+            const double gamma = ((double)j - 0.5 * (nb - 1)) * dg;
+            const double th = beta + M_PI + gamma;
+            const double ux = std::cos(th), uy = std::sin(th);
+            const double su = Sx * ux + Sy * uy;
+            // closest point to the image centre, pixel units, origin at the image corner
+            const double px = (Sx - su * ux) * inv_dx + 0.5 * n, py = (Sy - su * uy) * inv_dx + 0.5 * n;
+            hray[(size_t)v * nb + j] = make_ray_fx(px, py, ux, uy, n);
+        }
+    }
+    const double c0 = M_PI / ((double)V * g.pixel_mm * g.pixel_mm);
+    double diag = 0.0;   // h[0] + 2 sum_{odd m < nb} h[m]: the difference form's centre weight
+    for (int k = nb - 1; k >= 0; --k) {
+        const double h = k == 0 ? 0.25 : (k % 2 ? -1.0 / (M_PI * M_PI * (double)k * (double)k) : 0.0);
+        htaps[k] = (float)(c0 * h);
+        diag += k == 0 ? h : 2.0 * h;
+    }
+    s.ramp_diag = (float)(c0 * diag);
+    // nearest approach of a pixel centre to a source, in pixels
+    const double l_min = (g.dso_mm - g.n * g.pixel_mm / std::sqrt(2.0)) / g.pixel_mm;
+    s.half_k = (float)(1.002 / (1.0 - 0.75 / l_min));
+    cudaError_t e = cudaMemcpy(ray, hray.data(), rays * sizeof(RayFx), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(view, hview.data(), V * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(taps, htaps.data(), nb * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(cg, 0, sizeof(CgState));
+    if (e != cudaSuccess) {
+        cudaFree(mem);
+        return fail(AIR_ERR_CUDA, std::string("plan table upload: ") + cudaGetErrorString(e));
+    }
+    s.ray = ray;
+    s.view = view;
+    s.taps = taps;
+    s.x = x; s.r = r; s.p = p; s.q = q; s.rhs0 = rhs0; s.g = gg; s.b = b; s.b2 = b2; s.xt = xt;
+    s.z = z; s.zc = zc; s.y = ybuf;
+    s.cg = cg;
+    s.partial = partial;
+    s.mu = 1.f;
+    s.tau = 0.f;
+    P->geom = g;
+    P->desc = s;
+    P->mem = mem;
+    P->bytes = total;
+    P->ybuf = ybuf;
+    P->xbuf = xbuf;
+    cudaGetDevice(&P->device);
+    if (g.precision == AIR_PREC_BF16X3) {
+        air_status st = ramp_tc_create(P);
+        if (st != AIR_OK) {
+            cudaFree(mem);
+            return st;
+        }
+    }
+    return AIR_OK;
+}
+
+extern "C" const char *air_last_error(void) { return g_err.c_str(); }
+
+extern "C" air_status air_plan_create(const air_geometry *geom, air_plan **out) {
+    if (!out) return fail(AIR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    air_status st = validate_geometry(geom);
+    if (st != AIR_OK) return st;
+    air_plan *P = new (std::nothrow) air_plan();
+    if (!P) return fail(AIR_ERR_OOM, "host allocation failed");
+    st = plan_build(geom, P);
+    if (st != AIR_OK) {
+        delete P;
+        return st;
+    }
+    *out = P;
+    return AIR_OK;
+}
+
+extern "C" air_status air_plan_destroy(air_plan *P) {
+    if (!P) return AIR_OK;
+    ramp_tc_destroy(P);
+    if (P->mem) cudaFree(P->mem);
+    delete P;
+    return AIR_OK;
+}
+
+extern "C" size_t air_plan_bytes(const air_plan *P) { return P ? P->bytes + P->tc_bytes : 0; }
+
+// ------------------------------------------------------- stand-alone ops
+#define TRY(expr)                                   \
+    do {                                            \
+        air_status st_ = (expr);                    \
+        if (st_ != AIR_OK) return st_;              \
+    } while (0)
+#define CUDA_TRY(expr)                                                                           \
+    do {                                                                                         \
+        cudaError_t e_ = (expr);                                                                 \
+        if (e_ != cudaSuccess) return fail(AIR_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static size_t img_bytes(const air_plan *P) { return (size_t)P->geom.n * P->geom.n * 4; }
+static size_t sino_bytes(const air_plan *P) { return (size_t)P->geom.n_views * P->geom.n_bins * 4; }
+
+namespace air {
+// Z = C Y into dst (plan precision), from src (device).
+air_status apply_filter(const air_plan *P, const SliceDesc &base, const float *src, float *dst,
+                        cudaStream_t st) {
+    if (P->geom.precision == AIR_PREC_BF16X3 && P->geom.filter == AIR_FILTER_RAMLAK)
+        return ramp_tc_apply(P, src, dst, base.cg, 0, st);
+    SliceDesc s = base;
+    s.ext_in = src;
+    s.ext_out = dst;
+    CUDA_TRY(launch_op(OP_RAMP, s, RSRC_EXT, st));
+    return AIR_OK;
+}
+}  // namespace air
+
+extern "C" air_status air_project(const air_plan *P, const float *X, float *Y, air_stream stream) {
+    if (!P) return fail(AIR_ERR_INVALID_ARG, "plan is NULL");
+    TRY(check_dev_ptr(X, "X"));
+    TRY(check_dev_ptr(Y, "Y"));
+    if (overlap(X, img_bytes(P), Y, sino_bytes(P))) return fail(AIR_ERR_INVALID_ARG, "X and Y overlap");
+    SliceDesc s = P->desc;
+    s.ext_in = X;
+    s.ext_out = Y;
+    CUDA_TRY(launch_op(OP_TRANSPOSE, s, SRC_EXT, (cudaStream_t)stream));
+    CUDA_TRY(launch_op(OP_FWD, s, SRC_EXT, (cudaStream_t)stream));
+    return AIR_OK;
+}
+
+extern "C" air_status air_filter(const air_plan *P, const float *Y, float *Z, air_stream stream) {
+    if (!P) return fail(AIR_ERR_INVALID_ARG, "plan is NULL");
+    TRY(check_dev_ptr(Y, "Y"));
+    TRY(check_dev_ptr(Z, "Z"));
+    if (overlap(Y, sino_bytes(P), Z, sino_bytes(P))) return fail(AIR_ERR_INVALID_ARG, "Y and Z overlap");
+    return apply_filter(P, P->desc, Y, Z, (cudaStream_t)stream);
+}
+
+extern "C" air_status air_backproject(const air_plan *P, const float *Y, float *X, air_stream stream) {
+    if (!P) return fail(AIR_ERR_INVALID_ARG, "plan is NULL");
+    TRY(check_dev_ptr(Y, "Y"));
+    TRY(check_dev_ptr(X, "X"));
+    if (overlap(X, img_bytes(P), Y, sino_bytes(P))) return fail(AIR_ERR_INVALID_ARG, "X and Y overlap");
+    SliceDesc s = P->desc;
+    s.ext_in = Y;
+    s.ext_out = X;
+    CUDA_TRY(launch_op(OP_BWD, s, BWD_PLAIN, (cudaStream_t)stream));
+    return AIR_OK;
+}
+
+extern "C" air_status air_filtered_backproject(const air_plan *P, const float *Y, float *X,
+                                               air_stream stream) {
+    if (!P) return fail(AIR_ERR_INVALID_ARG, "plan is NULL");
+    TRY(check_dev_ptr(Y, "Y"));
+    TRY(check_dev_ptr(X, "X"));
+    if (overlap(X, img_bytes(P), Y, sino_bytes(P))) return fail(AIR_ERR_INVALID_ARG, "X and Y overlap");
+    const cudaStream_t st = (cudaStream_t)stream;
+    TRY(apply_filter(P, P->desc, Y, P->desc.zc, st));
+    SliceDesc s = P->desc;
+    s.ext_in = P->desc.zc;
+    s.ext_out = X;
+    CUDA_TRY(launch_op(OP_BWD, s, BWD_PLAIN, st));
+    return AIR_OK;
+}
+
+extern "C" air_status air_framelet(const air_plan *P, const float *in, float *out, int adjoint,
+                                   air_stream stream) {
+    if (!P) return fail(AIR_ERR_INVALID_ARG, "plan is NULL");
+    TRY(check_dev_ptr(in, "in"));
+    TRY(check_dev_ptr(out, "out"));
+    const size_t bi = adjoint ? 9 * img_bytes(P) : img_bytes(P);
+    const size_t bo = adjoint ? img_bytes(P) : 9 * img_bytes(P);
+    if (overlap(in, bi, out, bo)) return fail(AIR_ERR_INVALID_ARG, "in and out overlap");
+    SliceDesc s = P->desc;
+    s.ext_in = in;
+    s.ext_out = out;
+    CUDA_TRY(launch_op(adjoint ? OP_FRAMELET_T : OP_FRAMELET, s, 0, (cudaStream_t)stream));
+    return AIR_OK;
+}
+
+extern "C" air_status air_shrink(const air_plan *P, const float *X, float *b, float *g, float thresh,
+                                 double *resid, air_stream stream) {
+    if (!P) return fail(AIR_ERR_INVALID_ARG, "plan is NULL");
+    TRY(check_dev_ptr(X, "X"));
+    TRY(check_dev_ptr(b, "b"));
+    TRY(check_dev_ptr(g, "g"));
+    if (resid) TRY(check_dev_ptr(resid, "resid"));
+    if (!(thresh >= 0.f) || !std::isfinite(thresh)) return fail(AIR_ERR_INVALID_ARG, "thresh must be >= 0");
+    const size_t ib = img_bytes(P);
+    if (overlap(X, ib, b, 9 * ib) || overlap(X, ib, g, ib) || overlap(b, 9 * ib, g, ib))
+        return fail(AIR_ERR_INVALID_ARG, "X, b and g must not overlap");
+    const cudaStream_t st = (cudaStream_t)stream;
+    SliceDesc s = P->desc;
+    s.ext_in = X;
+    s.ext_out = b;
+    s.ext_out2 = g;
+    s.tau = thresh;
+    s.ext_scalar = resid;
+    s.resid_out = nullptr;
+    CUDA_TRY(launch_op(OP_SHRINK, s, 2, st));
+    CUDA_TRY(cudaMemcpyAsync(b, P->desc.b2, 9 * ib, cudaMemcpyDeviceToDevice, st));
+    return AIR_OK;
+}
+
+// ------------------------------------------------------------------ solve
+namespace air {
+
+// The split-Bregman program of one slice as a list of phases.
+std::vector<Phase> solve_program(int n_outer, int n_cg, bool tc_ramp) {
+    std::vector<Phase> prog;
+    const int ramp = tc_ramp ? OP_RAMP_TC : OP_RAMP;
+    prog.push_back({ramp, RSRC_Y});        // zc = C y
+    prog.push_back({OP_BWD, BWD_RHS0});   // rhs0 = A^T zc
+    prog.push_back({OP_ZERO, 0});         // X = 0, b = 0, g = 0
+    for (int k = 0; k < n_outer; ++k) {
+        prog.push_back({OP_TRANSPOSE, SRC_X});        // r = rhs0 + mu g - M x, p = r
+        prog.push_back({OP_FWD, SRC_X});
+        prog.push_back({ramp, RSRC_Z});
+        prog.push_back({OP_BWD, BWD_RESID});
+        for (int i = 0; i < n_cg; ++i) {
+            prog.push_back({OP_TRANSPOSE, SRC_P});    // q = M p
+            prog.push_back({OP_FWD, SRC_P});
+            prog.push_back({ramp, RSRC_Z});
+            prog.push_back({OP_BWD, BWD_Q});
+            prog.push_back({OP_CG_A, 0});
+            prog.push_back({OP_CG_B, 0});
+        }
+        prog.push_back({OP_SHRINK, k & 1});
+    }
+    return prog;
+}
+
+air_status run_program_single(const air_plan *P, const SliceDesc &s, const std::vector<Phase> &prog,
+                              cudaStream_t st) {
+    for (const Phase &ph : prog) {
+        if (ph.op == OP_RAMP_TC) {
+            const float *src = ph.arg == RSRC_Y ? s.y : s.z;
+            TRY(ramp_tc_apply(P, src, s.zc, s.cg, ph.arg == RSRC_Z, st));
+        } else {
+            CUDA_TRY(launch_op(ph.op, s, ph.arg, st));
+        }
+    }
+    return AIR_OK;
+}
+
+air_status check_solve_args(const air_plan *P, const float *Y, float lambda, float mu, int n_outer,
+                            int n_cg, const float *X) {
+    if (!P) return fail(AIR_ERR_INVALID_ARG, "plan is NULL");
+    if (!(mu > 0.f) || !std::isfinite(mu)) return fail(AIR_ERR_INVALID_ARG, "mu must be > 0");
+    if (!(lambda >= 0.f) || !std::isfinite(lambda)) return fail(AIR_ERR_INVALID_ARG, "lambda must be >= 0");
+    if (n_outer < 0 || n_cg < 0 || n_outer > 100000 || n_cg > 100000)
+        return fail(AIR_ERR_INVALID_ARG, "n_outer and n_cg must be in 0..100000");
+    if (Y && X && overlap(X, img_bytes(P), Y, sino_bytes(P)))
+        return fail(AIR_ERR_INVALID_ARG, "X and Y overlap");
+    return AIR_OK;
+}
+
+SliceDesc solve_desc(const air_plan *P, const float *Y, float lambda, float mu, float *X, double *resid) {
+    SliceDesc s = P->desc;
+    s.y = Y;
+    s.x = X;
+    s.mu = mu;
+    s.tau = lambda / mu;
+    s.resid_out = resid;
+    return s;
+}
+
+}  // namespace air
+
+extern "C" air_status air_solve(const air_plan *P, const float *Y, float lambda, float mu, int n_outer,
+                                int n_cg, float *X, double *resid, air_stream stream) {
+    TRY(check_solve_args(P, Y, lambda, mu, n_outer, n_cg, X));
+    TRY(check_dev_ptr(Y, "Y"));
+    TRY(check_dev_ptr(X, "X"));
+    if (resid) TRY(check_dev_ptr(resid, "resid"));
+    const bool tc = P->geom.precision == AIR_PREC_BF16X3 && P->geom.filter == AIR_FILTER_RAMLAK;
+    SliceDesc s = solve_desc(P, Y, lambda, mu, X, resid);
+    return run_program_single(P, s, solve_program(n_outer, n_cg, tc), (cudaStream_t)stream);
+}
+
+extern "C" air_status air_solve_host(const air_plan *P, const float *Y_host, float lambda, float mu,
+                                     int n_outer, int n_cg, float *X_host, air_stream stream) {
+    TRY(check_solve_args(P, nullptr, lambda, mu, n_outer, n_cg, nullptr));
+    if (!Y_host || !X_host) return fail(AIR_ERR_INVALID_ARG, "Y_host and X_host must not be NULL");
+    const cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(P->ybuf, Y_host, sino_bytes(P), cudaMemcpyHostToDevice, st));
+    const bool tc = P->geom.precision == AIR_PREC_BF16X3 && P->geom.filter == AIR_FILTER_RAMLAK;
+    SliceDesc s = solve_desc(P, P->ybuf, lambda, mu, P->xbuf, nullptr);
+    TRY(run_program_single(P, s, solve_program(n_outer, n_cg, tc), st));
+    CUDA_TRY(cudaMemcpyAsync(X_host, P->xbuf, img_bytes(P), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return AIR_OK;
+}

@@ -1,0 +1,191 @@
+// Kernels of the AIR hot path (sm_103a): per-op kernels over one slice, the
+// task-table kernel over many slices, and the persistent batch kernel.
+#include "launch.h"
+#include "tiles.cuh"
+
+namespace air {
+
+// ------------------------------------------------------------------------
+// per-op kernels: one block per tile of one slice
+// ------------------------------------------------------------------------
+template <int OP>
+__global__ void __launch_bounds__(AIR_THREADS) k_op(const SliceDesc s, int arg) {
+    extern __shared__ __align__(16) float sm[];
+    const int tile = blockIdx.x;
+    if constexpr (OP == OP_FWD) {
+        tile_fwd(s, arg, tile);
+    } else if constexpr (OP == OP_RAMP) {
+        tile_ramp(s, arg, tile, sm);
+    } else if constexpr (OP == OP_BWD) {
+        tile_bwd(s, arg, tile);
+    } else if constexpr (OP == OP_CG_A) {
+        tile_cg_a(s, tile);
+    } else if constexpr (OP == OP_CG_B) {
+        tile_cg_b(s, tile);
+    } else if constexpr (OP == OP_ZERO) {
+        tile_zero(s, tile);
+    } else if constexpr (OP == OP_SHRINK) {
+        if (arg < 2) {
+            ShrinkArgs a{s.x, arg ? s.b2 : s.b, arg ? s.b : s.b2, s.g, s.tau};
+            tile_shrink(s, a, tile, true, nullptr, sm);
+        } else {  // stand-alone call: X, b (read), scratch b', g from the ext operands
+            ShrinkArgs a{s.ext_in, s.ext_out, s.b2, s.ext_out2, s.tau};
+            tile_shrink(s, a, tile, true, s.ext_scalar, sm);
+        }
+    } else if constexpr (OP == OP_FRAMELET) {
+        tile_framelet(s, arg, tile, sm);
+    } else if constexpr (OP == OP_TRANSPOSE) {
+        tile_transpose(s, arg, tile, sm);
+    }
+}
+
+template <int OP>
+static cudaError_t launch_one(const SliceDesc &s, int arg, cudaStream_t st) {
+    const int tiles = tiles_of(s, OP == OP_FRAMELET && arg ? OP_FRAMELET_T : OP);
+    if (tiles <= 0) return cudaSuccess;
+    const size_t smem = tile_smem(s, OP);
+    static bool attr_done = false;   // opt in to > 48 KB dynamic shared memory once
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(k_op<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    k_op<OP><<<tiles, AIR_THREADS, smem, st>>>(s, arg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_op(int op, const SliceDesc &s, int arg, cudaStream_t st) {
+    switch (op) {
+    case OP_FWD: return launch_one<OP_FWD>(s, arg, st);
+    case OP_RAMP: return launch_one<OP_RAMP>(s, arg, st);
+    case OP_BWD: return launch_one<OP_BWD>(s, arg, st);
+    case OP_CG_A: return launch_one<OP_CG_A>(s, arg, st);
+    case OP_CG_B: return launch_one<OP_CG_B>(s, arg, st);
+    case OP_ZERO: return launch_one<OP_ZERO>(s, arg, st);
+    case OP_SHRINK: return launch_one<OP_SHRINK>(s, arg, st);
+    case OP_FRAMELET: return launch_one<OP_FRAMELET>(s, 0, st);
+    case OP_FRAMELET_T: return launch_one<OP_FRAMELET>(s, 1, st);
+    case OP_TRANSPOSE: return launch_one<OP_TRANSPOSE>(s, arg, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// ------------------------------------------------------------------------
+// task-table kernel: block -> (task, tile) by binary search over tile0
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(AIR_THREADS)
+k_tasks(const SliceDesc *__restrict__ slices, const Task *__restrict__ tasks, int ntasks) {
+    extern __shared__ __align__(16) float sm[];
+    const int b = blockIdx.x;
+    int lo = 0, hi = ntasks - 1;
+    while (lo < hi) {                 // last task with tile0 <= b
+        const int mid = (lo + hi + 1) >> 1;
+        if (tasks[mid].tile0 <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const Task t = tasks[lo];
+    run_tile(slices[t.slice], t.op, t.arg, b - t.tile0, sm);
+}
+
+cudaError_t launch_tasks(const SliceDesc *d_slices, const Task *d_tasks, int ntasks,
+                         int total_tiles, size_t smem, cudaStream_t st) {
+    if (ntasks <= 0 || total_tiles <= 0) return cudaSuccess;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(k_tasks, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    k_tasks<<<total_tiles, AIR_THREADS, smem, st>>>(d_slices, d_tasks, ntasks);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// persistent batch kernel with a bounded grid barrier
+// ------------------------------------------------------------------------
+// Spin budget of one barrier wait: 2^25 polls with a 128 ns back-off, a few
+// seconds, far above any phase; on expiry the block records AIR_ERR_TIMEOUT
+// and every block leaves at its next barrier.
+constexpr long long BARRIER_POLLS = 1ll << 25;
+
+__device__ bool grid_barrier(BatchCtl *ctl) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &ctl->gen;
+        volatile int *verr = &ctl->error;
+        const unsigned gen = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&ctl->arrive, 1u);
+        int good = 0;
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&ctl->arrive, 0u);
+            __threadfence();
+            atomicAdd(&ctl->gen, 1u);
+            good = *verr == 0;
+        } else {
+            for (long long it = 0; it < BARRIER_POLLS; ++it) {
+                if (*vgen != gen) { good = 1; break; }
+                if (*verr != 0) break;
+                __nanosleep(128);
+            }
+            if (!good && *verr == 0) atomicCAS(&ctl->error, 0, (int)AIR_ERR_TIMEOUT);
+            good = good && *verr == 0;
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__global__ void __launch_bounds__(AIR_THREADS)
+k_persistent(const SliceDesc *__restrict__ slices, int nslices, const Phase *__restrict__ prog,
+             int nphases, BatchCtl *ctl) {
+    extern __shared__ __align__(16) float sm[];
+    for (int ph = 0; ph < nphases; ++ph) {
+        int si = 0, base = 0;
+        int cur = nslices > 0 ? tiles_of(slices[0], prog[ph].op) : 0;
+        for (int t = blockIdx.x;; t += gridDim.x) {
+            while (si < nslices && t >= base + cur) {
+                base += cur;
+                ++si;
+                if (si < nslices) cur = tiles_of(slices[si], prog[(size_t)si * nphases + ph].op);
+            }
+            if (si >= nslices) break;
+            const Phase P = prog[(size_t)si * nphases + ph];
+            run_tile(slices[si], P.op, P.arg, t - base, sm);
+        }
+        if (!grid_barrier(ctl)) return;
+    }
+}
+
+int persistent_grid(size_t smem) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent, AIR_THREADS, smem) != cudaSuccess)
+        return 0;
+    return sms * per;
+}
+
+cudaError_t launch_persistent(const SliceDesc *d_slices, int nslices, const Phase *d_prog,
+                              int nphases, BatchCtl *d_ctl, int grid, size_t smem,
+                              cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(AIR_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_persistent, d_slices, nslices, d_prog, nphases, d_ctl);
+}
+
+}  // namespace air

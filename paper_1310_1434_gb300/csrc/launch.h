@@ -1,0 +1,36 @@
+// Host-side launchers of the AIR kernels (defined in kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "air_internal.cuh"
+
+namespace air {
+
+// One op over all tiles of one slice.
+cudaError_t launch_op(int op, const SliceDesc &s, int arg, cudaStream_t st);
+
+// One step of many (slice, op) tasks in a single launch; tasks[] and
+// slices[] are device arrays, total_tiles = sum of the tasks' tiles,
+// smem = the largest tile_smem() among them.
+cudaError_t launch_tasks(const SliceDesc *d_slices, const Task *d_tasks, int ntasks,
+                         int total_tiles, size_t smem, cudaStream_t st);
+
+// Persistent batch solve: one cooperative launch runs every phase of every
+// slice's program, with a bounded grid barrier between phases.
+struct Phase {
+    int op, arg;
+};
+struct BatchCtl {
+    unsigned arrive;     // grid barrier: blocks arrived in this generation
+    unsigned gen;        // grid barrier generation
+    int error;           // AIR_ERR_TIMEOUT if a barrier wait gave up
+    int pad;
+};
+cudaError_t launch_persistent(const SliceDesc *d_slices, int nslices, const Phase *d_prog,
+                              int nphases, BatchCtl *d_ctl, int grid, size_t smem,
+                              cudaStream_t st);
+// Largest co-resident grid of the persistent kernel for the given smem.
+int persistent_grid(size_t smem);
+
+}  // namespace air

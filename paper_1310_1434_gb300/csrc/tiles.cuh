@@ -1,0 +1,577 @@
+// Tile functions of the AIR hot path.  One call = one thread block of
+// AIR_THREADS threads working on one tile of one slice.  See
+// air_internal.cuh for the launch forms that share them.
+#pragma once
+
+#include "air_internal.cuh"
+
+namespace air {
+
+// ======================================================================
+// Forward projector A (Eq. 1): Y_{v,j} = dx * sum_i l_ij X_i, l_ij the exact
+// length of ray (v,j) inside pixel i.  Ray-driven, one thread per ray.  The
+// ray is walked along its major axis one column (row) at a time; in column k
+// its span [lo, lo + Ma] (fixed point, 2^-32 px) touches one or two pixel
+// rows, whose lengths are the integer overlaps times c (see RayFx).  A ray
+// walking columns reads the transposed image so that the 32 neighbouring
+// rays of a warp read neighbouring addresses.
+// ======================================================================
+__device__ __forceinline__ float fx_len(unsigned long long ov, float c) {
+    return __fmul_rn(__ull2float_rn(ov), c);
+}
+
+__device__ __forceinline__ float fx_ray(const float *__restrict__ X, const float *__restrict__ XT, int n,
+                                        const RayFx &r) {
+    const int k0 = r.kk & 0xffff, k1 = r.kk >> 16;
+    const float *__restrict__ src = r.o ? XT : X;     // row k of src = column (row) k of the walk
+    const long long M = r.M;
+    const unsigned Ma = r.Ma;
+    const float c = r.c;
+    long long lo = r.L0 + (long long)k0 * M;
+    float acc = 0.f;
+#pragma unroll 2
+    for (int k = k0; k < k1; ++k) {
+        const long long hi = lo + (long long)Ma;
+        const int r0 = (int)(lo >> 32);
+        const int r1 = (int)((hi - 1) >> 32);
+        const bool two = r1 != r0;
+        // overlap with row r0 and (when the span crosses a row boundary) r1
+        const unsigned ov0 = two ? 0u - (unsigned)lo : Ma;
+        const unsigned ov1 = two ? (unsigned)hi : 0u;
+        const float *__restrict__ row = src + (size_t)k * n;
+        if ((unsigned)r0 < (unsigned)n) acc = fmaf(fx_len(ov0, c), __ldg(row + r0), acc);
+        if (two && (unsigned)r1 < (unsigned)n) acc = fmaf(fx_len(ov1, c), __ldg(row + r1), acc);
+        lo += M;
+    }
+    return acc;
+}
+
+__device__ __forceinline__ void tile_fwd(const SliceDesc &s, int arg, int tile) {
+    if (arg == SRC_P && s.cg->stop) return;
+    const float *src = arg == SRC_X ? s.x : (arg == SRC_P ? s.p : s.ext_in);
+    float *dst = arg == SRC_EXT ? s.ext_out : s.z;
+    const int idx = tile * AIR_THREADS + threadIdx.x;
+    if (idx >= s.V * s.nb) return;
+    const RayFx r = s.ray[idx];
+    dst[idx] = s.dx * fx_ray(src, s.xt, s.n, r);
+}
+
+// xt = transpose(src), 32 x 32 tiles through shared memory (runs before
+// every projection: rays that walk columns read xt).
+__device__ __forceinline__ void tile_transpose(const SliceDesc &s, int arg, int tile, float *sm) {
+    if (arg == SRC_P && s.cg->stop) return;
+    const float *src = arg == SRC_X ? s.x : (arg == SRC_P ? s.p : s.ext_in);
+    const int n = s.n, tpr = (n + 31) / 32;
+    const int x0 = (tile % tpr) * 32, y0 = (tile / tpr) * 32;
+    float(*t)[33] = reinterpret_cast<float(*)[33]>(sm);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int yy = ty; yy < 32; yy += AIR_THREADS / 32)
+        if (y0 + yy < n && x0 + tx < n) t[yy][tx] = src[(size_t)(y0 + yy) * n + x0 + tx];
+    __syncthreads();
+    for (int xx = ty; xx < 32; xx += AIR_THREADS / 32)
+        if (x0 + xx < n && y0 + tx < n) s.xt[(size_t)(x0 + xx) * n + y0 + tx] = t[tx][xx];
+    __syncthreads();
+}
+
+// ======================================================================
+// Backprojector A^T: gather per pixel over every view and every bin whose
+// ray meets the pixel.  The bins are found from the fan angle of the pixel
+// centre widened by the pixel's angular half-width and a margin; each
+// candidate's length is the exact integer overlap of its fixed-point span
+// with the pixel, the same number tile_fwd uses, so the sum is the exact
+// transpose of the projector without atomics.
+// ======================================================================
+// arctan(u) for |u| <= 0.45 by its Maclaurin (Gregory) series through u^13;
+// the alternating-series remainder is below 0.45^15/15 = 4.2e-7 rad, far
+// inside the margin of the bin search below.
+__device__ __forceinline__ float atan_series(float u) {
+    const float w = u * u;
+    float p = 1.f / 13.f;
+    p = fmaf(p, w, -1.f / 11.f);
+    p = fmaf(p, w, 1.f / 9.f);
+    p = fmaf(p, w, -1.f / 7.f);
+    p = fmaf(p, w, 1.f / 5.f);
+    p = fmaf(p, w, -1.f / 3.f);
+    p = fmaf(p, w, 1.f);
+    return u * p;
+}
+
+// Sum over views v0, v0 + dv, ... of pixel (ix, iy)'s backprojection.
+__device__ __forceinline__ float bwd_pixel(const SliceDesc &s, const float *__restrict__ Z, int ix, int iy,
+                                           int v0, int dv) {
+    const float xc = (float)ix + 0.5f - s.half_n, yc = (float)iy + 0.5f - s.half_n;
+    const int nb = s.nb;
+    float acc = 0.f;
+#pragma unroll 1
+    for (int v = v0; v < s.V; v += dv) {
+        const float4 w = __ldg(s.view + v);
+        const float dxs = xc - w.x, dys = yc - w.y;
+        const float cr = w.z * dys - w.w * dxs;   // L sin(gamma): c x d
+        const float dt = w.z * dxs + w.w * dys;   // L cos(gamma): c . d  (> 0)
+        const float u = __fdividef(cr, dt);
+        const float gam = fabsf(u) <= 0.45f ? atan_series(u) : atan2f(cr, dt);
+        // half-width of the pixel's fan-angle footprint: sin(phi) <=
+        // (|dx|+|dy|)/2 / (L (L - 0.75)) <= (|dx|+|dy|)/2 / L^2 * half_k, with
+        // half_k = 1.002 / (1 - 0.75/L_min) covering asin and L >= L_min
+        const float half = 0.5f * (fabsf(dxs) + fabsf(dys)) * __fdividef(s.half_k, fmaf(dxs, dxs, dys * dys));
+        const float jc = fmaf(gam, s.inv_dgamma, s.jmid);
+        const float hw = fmaf(half, s.inv_dgamma, 0.02f);
+        const int jlo = max(0, (int)ceilf(jc - hw));
+        const int jhi = min(nb - 1, (int)floorf(jc + hw));
+        const RayFx *rr = s.ray + (size_t)v * nb;
+        const float *zz = Z + (size_t)v * nb;
+        for (int j = jlo; j <= jhi; ++j) {
+            const RayFx r = rr[j];
+            const int k = r.o ? ix : iy, rw = r.o ? iy : ix;
+            const long long lo = r.L0 + (long long)k * r.M;
+            const long long hi = lo + (long long)r.Ma;
+            const long long rb = (long long)rw << 32;
+            const long long a = lo > rb ? lo : rb;
+            const long long b = hi < rb + (1ll << 32) ? hi : rb + (1ll << 32);
+            if (b > a) acc = fmaf(fx_len((unsigned long long)(b - a), r.c), __ldg(zz + j), acc);
+        }
+    }
+    return acc;
+}
+
+// Sum `val` (valid in thread 0) of this tile into the slice's partials; the
+// tile that completes the phase sums all partials in a fixed order and gets
+// true with the total in *total (thread 0 only).
+__device__ __forceinline__ bool reduce_tiles(const SliceDesc &s, int tile, int ntiles, double val,
+                                             double *sh, double *total) {
+    __shared__ int last;
+    if (threadIdx.x == 0) {
+        s.partial[tile] = val;
+        __threadfence();
+        const unsigned prev = atomicAdd(&s.cg->counter, 1u);
+        last = prev == (unsigned)(ntiles - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double v = 0.0;
+    for (int i = threadIdx.x; i < ntiles; i += AIR_THREADS) v += __ldcg(s.partial + i);
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+        *total = v;
+        s.cg->counter = 0u;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile) {
+    __shared__ double sh[AIR_THREADS / 32];
+    __shared__ float red[BWD_GROUPS][BWD_TX * BWD_TY];
+    if (mode == BWD_Q && s.cg->stop) return;
+    const int tx = (s.n + BWD_TX - 1) / BWD_TX;
+    const int pix = threadIdx.x % (BWD_TX * BWD_TY), grp = threadIdx.x / (BWD_TX * BWD_TY);
+    const int ix = (tile % tx) * BWD_TX + pix % BWD_TX;
+    const int iy = (tile / tx) * BWD_TY + pix / BWD_TX;
+    const bool inside = ix < s.n && iy < s.n;
+    const float *Z = mode == BWD_PLAIN ? s.ext_in : s.zc;
+    red[grp][pix] = inside ? bwd_pixel(s, Z, ix, iy, grp, BWD_GROUPS) : 0.f;
+    __syncthreads();
+    // view groups summed in a fixed order; the epilogue runs on group 0
+    const bool in = inside && grp == 0;
+    float acc = 0.f;
+    if (in) {
+#pragma unroll
+        for (int k = 0; k < BWD_GROUPS; ++k) acc += red[k][pix];
+        acc *= s.dx;
+    }
+    __syncthreads();   // red is reused by the next tile of a persistent block
+    const int i = iy * s.n + ix;
+    if (mode == BWD_PLAIN) {
+        if (in) s.ext_out[i] = acc;
+        return;
+    }
+    if (mode == BWD_RHS0) {
+        if (in) s.rhs0[i] = acc;
+        return;
+    }
+    double part = 0.0;
+    if (mode == BWD_RESID) {
+        if (in) {
+            const float mx = fmaf(s.mu, s.x[i], acc);
+            const float rv = fmaf(s.mu, s.g[i], s.rhs0[i]) - mx;
+            s.r[i] = rv;
+            s.p[i] = rv;
+            part = (double)rv * (double)rv;
+        }
+    } else {  // BWD_Q
+        if (in) {
+            const float pv = s.p[i];
+            const float qv = fmaf(s.mu, pv, acc);
+            s.q[i] = qv;
+            part = (double)pv * (double)qv;
+        }
+    }
+    part = block_sum(part, sh);
+    double tot;
+    if (reduce_tiles(s, tile, tiles_bwd(s), part, sh, &tot) && threadIdx.x == 0) {
+        CgState *c = s.cg;
+        if (mode == BWD_RESID) {
+            c->rho = tot;
+            c->stop = !(tot != 0.0);
+        } else {
+            c->pq = tot;
+            if (!(tot > 0.0)) c->stop = 1;
+            else c->alpha = c->rho / tot;
+        }
+    }
+}
+
+// ======================================================================
+// Ramp filtration C (Eq. 2), FP32 on the CUDA cores.  Per view, with taps =
+// c0 h (h[0] = 1/4, h[odd m] = -1/(pi m)^2) and samples outside the detector
+// zero (a linear convolution):
+//   Z[j] = taps[0] Y[j] + sum_{odd m} taps[m] (Y[j-m] + Y[j+m]).
+// Evaluated in the algebraically equal DIFFERENCE form
+//   Z[j] = diag Y[j] + sum_{odd m} taps[m] ((Y[j-m] - Y[j]) + (Y[j+m] - Y[j])),
+//   diag = taps[0] + 2 sum_{odd m < n_b} taps[m],
+// whose terms are differences of neighbouring samples instead of large
+// values that cancel (the ramp is a high-pass filter): it keeps the FP32
+// result within a few 1e-7 of the exact convolution where the direct form
+// loses two digits.  One view per tile; each thread owns RAMP_R consecutive
+// outputs and slides its left/right sample windows by two per tap.
+// ======================================================================
+constexpr int RAMP_R = 4;
+
+__device__ __forceinline__ void tile_ramp(const SliceDesc &s, int arg, int tile, float *sm) {
+    const float *src = arg == RSRC_Y ? s.y : (arg == RSRC_Z ? s.z : s.ext_in);
+    float *dst = arg == RSRC_EXT ? s.ext_out : s.zc;
+    const int nb = s.nb;
+    const size_t off = (size_t)tile * nb;
+    if (arg == RSRC_Z && s.cg->stop) return;
+    if (!s.filter) {
+        for (int j = threadIdx.x; j < nb; j += AIR_THREADS) dst[off + j] = src[off + j];
+        return;
+    }
+    // P[PO + k] = Y[k] for 0 <= k < nb, zero elsewhere.  The windows reach
+    // from j - (nb-1) - 2 (the prefetch after the last tap) to
+    // j + RAMP_R + nb, so the padding is nb + 2 on the left and nb + R + 4 on
+    // the right of any output j < nb.
+    const int PO = nb + 2;
+    const int plen = 3 * nb + 2 * RAMP_R + 4;
+    float *P = sm, *tp = sm + plen;
+    for (int k = threadIdx.x; k < plen; k += AIR_THREADS) {
+        const int i = k - PO;
+        P[k] = (i >= 0 && i < nb) ? src[off + i] : 0.f;
+    }
+    for (int k = threadIdx.x; k < nb; k += AIR_THREADS) tp[k] = __ldg(s.taps + k);
+    __syncthreads();
+    const float diag = s.ramp_diag;
+#pragma unroll 1
+    for (int j0 = threadIdx.x * RAMP_R; j0 < nb; j0 += AIR_THREADS * RAMP_R) {
+        const float *c = P + PO + j0;
+        float ctr[RAMP_R], L[RAMP_R], R[RAMP_R], acc[RAMP_R];
+#pragma unroll
+        for (int i = 0; i < RAMP_R; ++i) {
+            ctr[i] = c[i];
+            L[i] = c[i - 1];          // Y[j - m], m = 1
+            R[i] = c[i + 1];          // Y[j + m], m = 1
+            acc[i] = 0.f;
+        }
+#pragma unroll 2
+        for (int m = 1; m < nb; m += 2) {
+            const float h = tp[m];
+#pragma unroll
+            for (int i = 0; i < RAMP_R; ++i)
+                acc[i] = fmaf(h, __fadd_rn(__fsub_rn(L[i], ctr[i]), __fsub_rn(R[i], ctr[i])), acc[i]);
+            // slide to m + 2: left window moves down by two, right window up by two
+#pragma unroll
+            for (int i = RAMP_R - 1; i >= 2; --i) L[i] = L[i - 2];
+            L[1] = c[-m - 1];
+            L[0] = c[-m - 2];
+#pragma unroll
+            for (int i = 0; i < RAMP_R - 2; ++i) R[i] = R[i + 2];
+            R[RAMP_R - 2] = c[RAMP_R - 2 + m + 2];
+            R[RAMP_R - 1] = c[RAMP_R - 1 + m + 2];
+        }
+#pragma unroll
+        for (int i = 0; i < RAMP_R; ++i)
+            if (j0 + i < nb) dst[off + j0 + i] = fmaf(diag, ctr[i], acc[i]);
+    }
+    __syncthreads();
+}
+
+// ======================================================================
+// CG vector updates (Eq. 5 system) with FP64 inner products.
+// ======================================================================
+__device__ __forceinline__ void tile_cg_a(const SliceDesc &s, int tile) {
+    __shared__ double sh[AIR_THREADS / 32];
+    if (s.cg->stop) return;
+    const float a = (float)s.cg->alpha;
+    const int nn = s.n * s.n;
+    const int base = tile * VEC_PER_TILE;
+    double part = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = base + k * AIR_THREADS + threadIdx.x;
+        if (i < nn) {
+            s.x[i] = fmaf(a, s.p[i], s.x[i]);
+            const float rv = fmaf(-a, s.q[i], s.r[i]);
+            s.r[i] = rv;
+            part += (double)rv * (double)rv;
+        }
+    }
+    part = block_sum(part, sh);
+    double tot;
+    if (reduce_tiles(s, tile, tiles_vec(s), part, sh, &tot) && threadIdx.x == 0) {
+        CgState *c = s.cg;
+        c->beta = tot / c->rho;
+        c->rho = tot;
+        if (!(tot != 0.0)) c->stop = 1;
+    }
+}
+
+__device__ __forceinline__ void tile_cg_b(const SliceDesc &s, int tile) {
+    if (s.cg->stop) return;
+    const float bt = (float)s.cg->beta;
+    const int nn = s.n * s.n;
+    const int base = tile * VEC_PER_TILE;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = base + k * AIR_THREADS + threadIdx.x;
+        if (i < nn) s.p[i] = fmaf(bt, s.p[i], s.r[i]);
+    }
+}
+
+__device__ __forceinline__ void tile_zero(const SliceDesc &s, int tile) {
+    const int nn = s.n * s.n;
+    const int base = tile * VEC_PER_TILE;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = base + k * AIR_THREADS + threadIdx.x;
+        if (i < nn) {
+            s.x[i] = 0.f;
+            s.g[i] = 0.f;
+#pragma unroll
+            for (int band = 0; band < 9; ++band) s.b[(size_t)band * nn + i] = 0.f;
+        }
+    }
+    if (tile == 0 && threadIdx.x == 0) {
+        s.cg->stop = 0;
+        s.cg->outer = 0;
+        s.cg->counter = 0u;
+    }
+}
+
+// ======================================================================
+// Tensor framelet (piecewise-linear, one level, periodic) and the fused
+// split-Bregman shrink.  Taps at offsets -1, 0, +1:
+//   h0 = [1,2,1]/4, h1 = (sqrt2/4)[1,0,-1], h2 = [-1,2,-1]/4;
+//   (W_ab X)[y][x] = sum_{p,q} h_a[p] h_b[q] X[y+p][x+q]   (indices mod n)
+// ======================================================================
+__device__ __forceinline__ float ftap(int a, int p) {
+    const float s2 = 0.35355339059327373f;  // sqrt(2)/4
+    return a == 0 ? (p == 0 ? 0.5f : 0.25f) : (a == 1 ? (p == 0 ? 0.f : (p < 0 ? s2 : -s2)) : (p == 0 ? 0.5f : -0.25f));
+}
+
+__device__ __forceinline__ int wrapi(int v, int n) {
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+// W at one position from a 3x3 neighbourhood nb3[p+1][q+1] = X[y+p][x+q]
+__device__ __forceinline__ void framelet9(const float nb3[3][3], float out[9]) {
+    float rowf[3][3];  // rowf[b][p+1] = sum_q h_b[q] X[y+p][x+q]
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        rowf[0][p] = 0.25f * (nb3[p][0] + nb3[p][2]) + 0.5f * nb3[p][1];
+        rowf[1][p] = 0.35355339059327373f * (nb3[p][0] - nb3[p][2]);
+        rowf[2][p] = 0.5f * nb3[p][1] - 0.25f * (nb3[p][0] + nb3[p][2]);
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        out[0 * 3 + b] = 0.25f * (rowf[b][0] + rowf[b][2]) + 0.5f * rowf[b][1];
+        out[1 * 3 + b] = 0.35355339059327373f * (rowf[b][0] - rowf[b][2]);
+        out[2 * 3 + b] = 0.5f * rowf[b][1] - 0.25f * (rowf[b][0] + rowf[b][2]);
+    }
+}
+
+// W^T at one position of band c: sum_{p,q} h_a[p] h_b[q] C[y-p][x-q], with
+// e3[p+1][q+1] = C[y+p][x+q] (so offset -p is index 1-p).
+__device__ __forceinline__ float framelet_t1(int a, int b, const float e3[3][3]) {
+    float acc = 0.f;
+#pragma unroll
+    for (int p = -1; p <= 1; ++p) {
+        float rs = 0.f;
+#pragma unroll
+        for (int q = -1; q <= 1; ++q) rs = fmaf(ftap(b, q), e3[1 - p][1 - q], rs);
+        acc = fmaf(ftap(a, p), rs, acc);
+    }
+    return acc;
+}
+
+// The Bregman variable is double-buffered: a tile reads b in its halo,
+// which neighbouring tiles are updating, so the update reads b_in and writes
+// b_out (the solver alternates the two buffers between outer steps).
+struct ShrinkArgs {
+    const float *X;
+    const float *b_in;
+    float *b_out;
+    float *g;
+    float tau;
+};
+
+constexpr int SHR_H = SHR_T + 2;   // coefficient tile incl. halo 1
+constexpr int SHR_X = SHR_T + 4;   // image tile incl. halo 2
+
+// Shared-memory layout of the shrink tile (floats): X tile, then E[9][SHR_H^2]
+constexpr int SHR_SMEM_FLOATS = SHR_X * SHR_X + 9 * SHR_H * SHR_H;
+
+__device__ __forceinline__ void tile_shrink(const SliceDesc &s, const ShrinkArgs &A, int tile,
+                                            bool reduce, double *resid_dst, float *sm) {
+    __shared__ double sh[AIR_THREADS / 32];
+    const int n = s.n, nn = n * n;
+    const int tpr = (n + SHR_T - 1) / SHR_T;
+    const int x0 = (tile % tpr) * SHR_T, y0 = (tile / tpr) * SHR_T;
+    float *Xs = sm;                      // [SHR_X][SHR_X], origin (y0-2, x0-2)
+    float *E = sm + SHR_X * SHR_X;       // [9][SHR_H][SHR_H], origin (y0-1, x0-1)
+    for (int k = threadIdx.x; k < SHR_X * SHR_X; k += AIR_THREADS) {
+        const int ly = k / SHR_X, lx = k % SHR_X;
+        Xs[k] = A.X[wrapi(y0 - 2 + ly, n) * n + wrapi(x0 - 2 + lx, n)];
+    }
+    __syncthreads();
+    double part = 0.0;
+    for (int k = threadIdx.x; k < SHR_H * SHR_H; k += AIR_THREADS) {
+        const int cy = k / SHR_H, cx = k % SHR_H;
+        const int gy = wrapi(y0 - 1 + cy, n), gx = wrapi(x0 - 1 + cx, n);
+        const bool interior = cy >= 1 && cy <= SHR_T && cx >= 1 && cx <= SHR_T &&
+                              y0 - 1 + cy < n && x0 - 1 + cx < n;
+        float nb3[3][3];
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) nb3[p][q] = Xs[(cy + p) * SHR_X + cx + q];
+        float wx[9];
+        framelet9(nb3, wx);
+        const size_t gi = (size_t)gy * n + gx;
+#pragma unroll
+        for (int band = 0; band < 9; ++band) {
+            const float bo = A.b_in[(size_t)band * nn + gi];
+            const float t = wx[band] + bo;
+            float d = t;
+            if (band > 0) {
+                const float m = fabsf(t) - A.tau;
+                d = m > 0.f ? copysignf(m, t) : 0.f;
+            }
+            const float bn = t - d;
+            E[band * SHR_H * SHR_H + k] = d - bn;
+            if (interior) {
+                A.b_out[(size_t)band * nn + gi] = bn;
+                const double e = (double)wx[band] - (double)d;
+                part += e * e;
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < SHR_T * SHR_T; k += AIR_THREADS) {
+        const int ly = k / SHR_T, lx = k % SHR_T;
+        if (y0 + ly >= n || x0 + lx >= n) continue;
+        float acc = 0.f;
+#pragma unroll
+        for (int band = 0; band < 9; ++band) {
+            float e3[3][3];
+            const float *Eb = E + band * SHR_H * SHR_H;
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) e3[p][q] = Eb[(ly + p) * SHR_H + lx + q];
+            acc += framelet_t1(band / 3, band % 3, e3);
+        }
+        A.g[(size_t)(y0 + ly) * n + x0 + lx] = acc;
+    }
+    if (!reduce) {
+        __syncthreads();
+        return;
+    }
+    part = block_sum(part, sh);
+    double tot;
+    if (reduce_tiles(s, tile, tiles_shr(s), part, sh, &tot) && threadIdx.x == 0) {
+        const double rn = sqrt(tot);
+        CgState *c = s.cg;
+        c->resid = rn;
+        if (resid_dst) *resid_dst = rn;
+        if (s.resid_out) s.resid_out[c->outer] = rn;
+        c->outer += 1;
+    }
+    __syncthreads();
+}
+
+// out = W in (adjoint = 0) or W^T in (adjoint = 1), for the API call.
+__device__ __forceinline__ void tile_framelet(const SliceDesc &s, int adjoint, int tile, float *sm) {
+    const int n = s.n, nn = n * n;
+    const int tpr = (n + SHR_T - 1) / SHR_T;
+    const int x0 = (tile % tpr) * SHR_T, y0 = (tile / tpr) * SHR_T;
+    const float *in = s.ext_in;
+    float *out = s.ext_out;
+    const int bands = adjoint ? 9 : 1;
+    for (int k = threadIdx.x; k < bands * SHR_H * SHR_H; k += AIR_THREADS) {
+        const int band = k / (SHR_H * SHR_H), rem = k % (SHR_H * SHR_H);
+        const int ly = rem / SHR_H, lx = rem % SHR_H;
+        sm[k] = in[(size_t)band * nn + wrapi(y0 - 1 + ly, n) * n + wrapi(x0 - 1 + lx, n)];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < SHR_T * SHR_T; k += AIR_THREADS) {
+        const int ly = k / SHR_T, lx = k % SHR_T;
+        if (y0 + ly >= n || x0 + lx >= n) continue;
+        const size_t gi = (size_t)(y0 + ly) * n + x0 + lx;
+        if (!adjoint) {
+            float nb3[3][3], wx[9];
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) nb3[p][q] = sm[(ly + p) * SHR_H + lx + q];
+            framelet9(nb3, wx);
+#pragma unroll
+            for (int band = 0; band < 9; ++band) out[(size_t)band * nn + gi] = wx[band];
+        } else {
+            float acc = 0.f;
+#pragma unroll
+            for (int band = 0; band < 9; ++band) {
+                float e3[3][3];
+#pragma unroll
+                for (int p = 0; p < 3; ++p)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) e3[p][q] = sm[band * SHR_H * SHR_H + (ly + p) * SHR_H + lx + q];
+                acc += framelet_t1(band / 3, band % 3, e3);
+            }
+            out[gi] = acc;
+        }
+    }
+    __syncthreads();
+}
+
+// Dynamic shared memory (bytes) a tile of `op` needs for a slice.
+__host__ inline size_t tile_smem(const SliceDesc &s, int op) {
+    switch (op) {
+    case OP_RAMP: return sizeof(float) * (4 * (size_t)s.nb + 2 * RAMP_R + 4);
+    case OP_SHRINK: return sizeof(float) * SHR_SMEM_FLOATS;
+    case OP_FRAMELET: case OP_FRAMELET_T: return sizeof(float) * 9 * SHR_H * SHR_H;
+    case OP_TRANSPOSE: return sizeof(float) * 32 * 33;
+    default: return 0;
+    }
+}
+
+// One tile of any op (used by the task-table and persistent kernels).
+__device__ __forceinline__ void run_tile(const SliceDesc &s, int op, int arg, int tile, float *sm) {
+    switch (op) {
+    case OP_FWD: tile_fwd(s, arg, tile); break;
+    case OP_TRANSPOSE: tile_transpose(s, arg, tile, sm); break;
+    case OP_RAMP: tile_ramp(s, arg, tile, sm); break;
+    case OP_BWD: tile_bwd(s, arg, tile); break;
+    case OP_CG_A: tile_cg_a(s, tile); break;
+    case OP_CG_B: tile_cg_b(s, tile); break;
+    case OP_ZERO: tile_zero(s, tile); break;
+    case OP_SHRINK: {   // arg = parity of the outer step: b -> b2, then b2 -> b
+        ShrinkArgs a{s.x, arg ? s.b2 : s.b, arg ? s.b : s.b2, s.g, s.tau};
+        tile_shrink(s, a, tile, true, nullptr, sm);
+        break;
+    }
+    default: break;
+    }
+}
+
+}  // namespace air

@@ -63,7 +63,7 @@ class Workload:
     n_cg: int
 
 
-def _wl(name, n, px, V, nb, seed, ne, nd, I0, lam=0.01, mu=1.0, n_outer=30, n_cg=8, **kw):
+def _wl(name, n, px, V, nb, seed, ne, nd, I0, lam=3e-4, mu=1.0, n_outer=30, n_cg=8, **kw):
     return Workload(name, Geometry(n, px, V, nb, **kw), seed, ne, nd, I0, lam, mu, n_outer, n_cg)
 
 
