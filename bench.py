@@ -1,0 +1,411 @@
+"""AIR benchmark: 512 x 512 split-Bregman AIR reconstructions per second on GB300.
+
+Workload (the 512^2 configuration): 512 x 512 images of 0.8 mm pixels,
+equiangular fan beam (source-isocentre 850 mm, source-detector 1450 mm),
+738 bins, 800 views (full) and 200 views (25 %), seeded ellipse + disk
+phantoms with Poisson noise at 2e4 photons/ray, lambda = 3e-4, mu = 1,
+30 split-Bregman x 8 CG iterations.  One step = one batch of B slices (half
+800-view, half 200-view) solved by the persistent batched kernel
+(air_solve_batch).  value = slices/s on the device with inputs resident;
+e2e = the same with pinned host buffers copied in and out inside the timed
+region.  The batch's working set (~60 MB per slice) exceeds L2 and L2 is
+also flushed between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl air|reference]
+
+Under torchrun each rank solves its own batches (no collective on the data
+path: slices are independent) and rank 0 prints the JSON line with the max
+time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1310_1434_gb300 import inputs  # noqa: E402
+
+METRIC = "512^2 AIR slices/s (split-Bregman TF, 30x8, fan beam 738 bins, 800/200 views)"
+UNIT = "slices/s"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="air", choices=["air", "reference"])
+    ap.add_argument("--batch", type=int, default=8, help="slices per step (even: half 800, half 200 views)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", default=None, choices=["fwd", "bwd", "ramp", "shrink", "solve", "plain"],
+                    help="profiling mode: run one operator on the 512^2/800-view slice --reps times")
+    ap.add_argument("--reps", type=int, default=3)
+    return ap.parse_args()
+
+
+def run_kernel(args):
+    """Runs one operator of the hot path --reps times (for ncu captures)."""
+    import torch
+    from paper_1310_1434_gb300 import air
+    air.load()
+    w = inputs.AIR512_V800
+    g = w.geom
+    ell, _, Y = inputs.make_case(w)
+    X = inputs.rasterize(g, ell)
+    plan = air.Plan(g)
+    Yd = torch.as_tensor(Y.astype(np.float32).ravel(), device="cuda")
+    Xd = torch.as_tensor(X.astype(np.float32).ravel(), device="cuda")
+    Zd = torch.empty_like(Yd)
+    X2 = torch.empty_like(Xd)
+    b = torch.zeros(9 * g.n * g.n, device="cuda")
+    gg = torch.empty_like(Xd)
+    ops = {"fwd": lambda: air.air_project(plan, Xd, Zd),
+           "bwd": lambda: air.air_backproject(plan, Yd, X2),
+           "ramp": lambda: air.air_filter(plan, Yd, Zd),
+           "shrink": lambda: air.air_shrink(plan, Xd, b, gg, w.lam / w.mu),
+           "solve": lambda: air.air_solve(plan, Yd, w.lam, w.mu, w.n_outer, w.n_cg, X2),
+           "plain": lambda: air.air_solve(plan, Yd, w.lam, w.mu, 1, 2, X2)}
+    for _ in range(args.reps):
+        ops[args.kernel]()
+    torch.cuda.synchronize()
+    print(f"ran {args.kernel} x{args.reps}")
+
+
+def workloads(batch: int, rank: int):
+    out = []
+    for i in range(batch):
+        base = inputs.AIR512_V800 if i % 2 == 0 else inputs.AIR512_V200
+        seed = 1 + i // 2 + 1000 * rank
+        out.append(inputs.Workload(f"{base.name}_s{seed}", base.geom, seed, base.n_ellipses, base.n_disks,
+                                   base.photons, base.lam, base.mu, base.n_outer, base.n_cg))
+    return out
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            p = json.load(f)
+        return {"hbm_gbs": float(p["hbm_gbs"]), "bf16_tflops": float(p["bf16_tflops"]),
+                "sm_max_mhz": float(p.get("sm_max_mhz", 2070.0)), "src": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "src": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def events_time(torch, stream, fn, reps: int) -> float:
+    """Average ms of fn() over reps launches on `stream`, CUDA events on that stream."""
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def cpu_baseline(sample_cg_steps: int = 2):
+    """The FP64 oracle (as it stands) on this host: a bounded sample of one
+    800-view 512^2 slice -- A'^T Y once and sample_cg_steps CG steps -- scaled
+    to one full 30 x (8 + 1) operator-pair solve.  Returns slices/s."""
+    import oracle
+    w = inputs.AIR512_V800
+    og = oracle.Geometry(**{k: getattr(w.geom, k) for k in oracle.Geometry.__dataclass_fields__})
+    _, _, Y = inputs.make_case(w)
+    t = time.perf_counter()
+    rhs = oracle.filtered_backproject(og, Y)
+    t_rhs = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle.cg(og, rhs, w.mu, sample_cg_steps)   # 1 residual + sample_cg_steps operator pairs
+    t_cg = time.perf_counter() - t
+    t_pair = t_cg / (sample_cg_steps + 1)
+    t = time.perf_counter()
+    oracle.shrink(np.zeros((w.geom.n, w.geom.n)), np.zeros((9, w.geom.n, w.geom.n)), w.lam / w.mu)
+    t_shr = time.perf_counter() - t
+    t_solve = t_rhs + w.n_outer * ((w.n_cg + 1) * t_pair + t_shr)
+    return {"value": 1.0 / t_solve, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": (f"FP64 oracle, one 512^2/800-view slice: A'^T Y once, {sample_cg_steps} CG steps "
+                       f"(+ residual) and one shrink, {t_rhs + t_cg + t_shr:.1f} s, scaled to "
+                       f"{w.n_outer} x ({w.n_cg}+1) operator pairs + {w.n_outer} shrinks per slice"),
+            "seconds_per_slice": t_solve}
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the FP64 CPU oracle, timed on this host's cores."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    w = inputs.AIR512_V800
+    og = oracle.Geometry(**{k: getattr(w.geom, k) for k in oracle.Geometry.__dataclass_fields__})
+    _, _, Y = inputs.make_case(w)
+    rhs = oracle.filtered_backproject(og, Y)
+
+    def step():   # one CG step of the oracle: the bounded sample of one solve
+        t = time.perf_counter()
+        oracle.cg(og, rhs, w.mu, 0)        # residual: one A and one A'^T
+        return time.perf_counter() - t
+
+    for _ in range(args.warmup):
+        step()
+    ts = [step() for _ in range(args.steps)]
+    t_pair = float(np.mean(ts))
+    t_solve = w.n_outer * (w.n_cg + 1) * t_pair
+    value = 1.0 / t_solve
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_pair,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "air512_v800 (512x512, 0.8 mm, 738 bins, 800 views, 30x8)"},
+            "cpu_baseline": {"kind": "oracle", "cores": oracle.threads(), "value": value, "unit": UNIT,
+                             "sample": "one CG operator pair (A then A^T C) per step, scaled to 30 x (8+1) pairs"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if args.kernel:
+        run_kernel(args)
+        return
+    import torch
+    from paper_1310_1434_gb300 import air
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    air.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    B = max(2, args.batch)
+
+    # ---- inputs: seeded synthetic sinograms, resident on the device ----
+    ws = workloads(B, rank)
+    Yh = [inputs.make_case(w)[2].astype(np.float32).ravel() for w in ws]
+    Yd = [torch.as_tensor(y, device=dev) for y in Yh]
+    Xd = [torch.empty(w.geom.n ** 2, device=dev) for w in ws]
+    plans = [air.Plan(w.geom) for w in ws]
+    lam = [w.lam for w in ws]
+    mu = [w.mu for w in ws]
+    no = [w.n_outer for w in ws]
+    ncg = [w.n_cg for w in ws]
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)   # > L2 (129 MB)
+
+    def step():
+        air.air_solve_batch(plans, Yd, lam, mu, no, ncg, Xd)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs ----
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_ms = float(sum(ms))
+
+    # ---- e2e: pinned host buffers in and out inside the timed region ----
+    Yp = [torch.from_numpy(y).pin_memory() for y in Yh]
+    Xp = [torch.empty(w.geom.n ** 2, pin_memory=True) for w in ws]
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for yd, yp in zip(Yd, Yp):
+            yd.copy_(yp, non_blocking=True)
+        step()
+        for xp, xd in zip(Xp, Xd):
+            xp.copy_(xd, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1000 * (time.perf_counter() - t0))
+    clk = clocks.stop()
+    h2d = sum(y.nbytes for y in Yh)
+    d2h = sum(x.numel() * 4 for x in Xp)
+
+    # ---- plain single-slice path: one air_solve per slice, per-slice latency ----
+    lat = {800: [], 200: []}
+    for i in range(min(B, 4)):
+        w = ws[i]
+        for _ in range(2):
+            flush.zero_()
+            t = events_time(torch, stream, lambda: air.air_solve(plans[i], Yd[i], w.lam, w.mu, w.n_outer,
+                                                                  w.n_cg, Xd[i]), 1)
+            lat[w.geom.n_views].append(t)
+    plain_ms = [t for v in lat.values() for t in v]
+
+    # ---- dominant kernel: the backprojector on a 512^2/800 slice ----
+    p800 = plans[0]
+    g8 = ws[0].geom
+    zin = Yd[0]
+    xout = torch.empty(g8.n ** 2, device=dev)
+    air.air_backproject(p800, zin, xout)
+    t_bwd = events_time(torch, stream, lambda: air.air_backproject(p800, zin, xout), 20)
+    yout = torch.empty(g8.n_views * g8.n_bins, device=dev)
+    air.air_project(p800, Xd[0], yout)
+    t_fwd = events_time(torch, stream, lambda: air.air_project(p800, Xd[0], yout), 20)
+    alg_bytes = 4 * (g8.n ** 2 + g8.n_views * g8.n_bins)       # read Z + write X (fwd: read X + write Y)
+    peaks = load_peaks()
+    # issue-limited roofline of the backprojector: warp instructions per
+    # launch from the committed ncu capture of the same kernel and input
+    inst_per_launch = BWD_WARP_INST_512_V800
+    sm_mhz = clk.get("sm_mhz") or peaks["sm_max_mhz"]
+    issue_peak = 152 * 4 * peaks["sm_max_mhz"] * 1e6 / 1e9     # G warp-instructions/s at max clock
+
+    # ---- reduce over ranks (max time) ----
+    t_rank = torch.tensor([total_ms, float(np.sum(e2e_ms))], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
+    total_ms, e2e_total = float(t_rank[0]), float(t_rank[1])
+    slices = B * args.steps * world
+    value = slices / (total_ms / 1000.0)
+    e2e_value = slices / (e2e_total / 1000.0)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline()
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": max(3, args.warmup),
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "air512: 512x512 0.8 mm, 738 bins, 800 and 200 views, 30x8 split-Bregman",
+                   "slices_per_step": B, "views_mix": "half 800, half 200",
+                   "form": "air_solve_batch (persistent kernel, CUDA graph)",
+                   "l2": "flushed between timed steps (256 MB write); working set > L2",
+                   "parallelism": f"slices sharded over {world} GPU(s), no collective"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * 1,
+        "clocks": clk,
+        "plain_gpu": {"path": "air_solve, one slice at a time",
+                      "slices_per_s": 1000.0 * len(plain_ms) / sum(plain_ms),
+                      "p50_ms": float(np.percentile(plain_ms, 50)), "p99_ms": float(np.percentile(plain_ms, 99)),
+                      "ms_800_views": float(np.mean(lat[800])) if lat[800] else None,
+                      "ms_200_views": float(np.mean(lat[200])) if lat[200] else None},
+        "latency_batch": {"p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+                          "note": "every slice of a batch completes with the batch"},
+        "projector": {"fwd_ms": t_fwd, "bwd_ms": t_bwd, "alg_bytes": alg_bytes,
+                      "fwd_hbm_gbs": alg_bytes / (t_fwd * 1e-3) / 1e9,
+                      "bwd_hbm_gbs": alg_bytes / (t_bwd * 1e-3) / 1e9,
+                      "hbm_frac_of_measured": alg_bytes / (t_bwd * 1e-3) / 1e9 / peaks["hbm_gbs"]},
+        "roofline": {"kernel": "backprojector (k_op<OP_BWD>), 512^2 / 800 views",
+                     "bound": "alu",
+                     "achieved": inst_per_launch / (t_bwd * 1e-3) / 1e9 if inst_per_launch else None,
+                     "peak": issue_peak, "unit": "Gwarp-inst/s",
+                     "frac": (inst_per_launch / (t_bwd * 1e-3) / 1e9 / issue_peak) if inst_per_launch else None,
+                     "traffic": BWD_DRAM_BYTES_512_V800,
+                     "peak_src": "152 SMs x 4 issue/clk x max SM clock",
+                     "sm_mhz_under_load": sm_mhz},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# From the committed ncu capture of the backprojector on the 512^2/800-view
+# slice (profiles/): warp instructions and DRAM bytes per launch.  None until
+# captured for the current kernel.
+BWD_WARP_INST_512_V800 = 961_736_922
+BWD_DRAM_BYTES_512_V800 = 19_284_736
+
+if __name__ == "__main__":
+    main()

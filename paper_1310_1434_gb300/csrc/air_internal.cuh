@@ -129,7 +129,7 @@ constexpr int VEC_PER_TILE = AIR_THREADS * 4;   // elementwise ops: 4 per thread
 __host__ __device__ inline int tiles_vec(const SliceDesc &s) {
     return (s.n * s.n + VEC_PER_TILE - 1) / VEC_PER_TILE;
 }
-constexpr int SHR_T = 32;                      // shrink/framelet output tile
+constexpr int SHR_T = 16;                      // shrink/framelet output tile
 __host__ __device__ inline int tiles_shr(const SliceDesc &s) {
     return ((s.n + SHR_T - 1) / SHR_T) * ((s.n + SHR_T - 1) / SHR_T);
 }

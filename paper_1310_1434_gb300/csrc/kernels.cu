@@ -74,9 +74,27 @@ cudaError_t launch_op(int op, const SliceDesc &s, int arg, cudaStream_t st) {
 // ------------------------------------------------------------------------
 // task-table kernel: block -> (task, tile) by binary search over tile0
 // ------------------------------------------------------------------------
-__global__ void __launch_bounds__(AIR_THREADS)
+// The slice descriptor of the current tile is staged in shared memory: the
+// tile functions read its fields inside their loops, which from global
+// memory would cost a load each time.
+__device__ __forceinline__ const SliceDesc &stage_desc(const SliceDesc *__restrict__ slices, int si,
+                                                       SliceDesc *sd, int *staged) {
+    if (*staged != si) {
+        __syncthreads();
+        const int words = (int)(sizeof(SliceDesc) / sizeof(int));
+        const int *src = reinterpret_cast<const int *>(slices + si);
+        int *dst = reinterpret_cast<int *>(sd);
+        for (int i = threadIdx.x; i < words; i += AIR_THREADS) dst[i] = src[i];
+        __syncthreads();
+        *staged = si;
+    }
+    return *sd;
+}
+
+__global__ void __launch_bounds__(AIR_THREADS, 5)
 k_tasks(const SliceDesc *__restrict__ slices, const Task *__restrict__ tasks, int ntasks) {
     extern __shared__ __align__(16) float sm[];
+    __shared__ __align__(16) SliceDesc sd;
     const int b = blockIdx.x;
     int lo = 0, hi = ntasks - 1;
     while (lo < hi) {                 // last task with tile0 <= b
@@ -85,7 +103,8 @@ k_tasks(const SliceDesc *__restrict__ slices, const Task *__restrict__ tasks, in
         else hi = mid - 1;
     }
     const Task t = tasks[lo];
-    run_tile(slices[t.slice], t.op, t.arg, b - t.tile0, sm);
+    int staged = -1;
+    run_tile(stage_desc(slices, t.slice, &sd, &staged), t.op, t.arg, b - t.tile0, sm);
 }
 
 cudaError_t launch_tasks(const SliceDesc *d_slices, const Task *d_tasks, int ntasks,
@@ -141,22 +160,24 @@ __device__ bool grid_barrier(BatchCtl *ctl) {
     return ok != 0;
 }
 
-__global__ void __launch_bounds__(AIR_THREADS)
+__global__ void __launch_bounds__(AIR_THREADS, 5)
 k_persistent(const SliceDesc *__restrict__ slices, int nslices, const Phase *__restrict__ prog,
              int nphases, BatchCtl *ctl) {
     extern __shared__ __align__(16) float sm[];
+    __shared__ __align__(16) SliceDesc sd;
+    int staged = -1;                  // slice whose descriptor sd holds
     for (int ph = 0; ph < nphases; ++ph) {
         int si = 0, base = 0;
-        int cur = nslices > 0 ? tiles_of(slices[0], prog[ph].op) : 0;
+        int ntile = nslices > 0 ? tiles_of(slices[0], prog[ph].op) : 0;
         for (int t = blockIdx.x;; t += gridDim.x) {
-            while (si < nslices && t >= base + cur) {
-                base += cur;
+            while (si < nslices && t >= base + ntile) {
+                base += ntile;
                 ++si;
-                if (si < nslices) cur = tiles_of(slices[si], prog[(size_t)si * nphases + ph].op);
+                if (si < nslices) ntile = tiles_of(slices[si], prog[(size_t)si * nphases + ph].op);
             }
             if (si >= nslices) break;
             const Phase P = prog[(size_t)si * nphases + ph];
-            run_tile(slices[si], P.op, P.arg, t - base, sm);
+            run_tile(stage_desc(slices, si, &sd, &staged), P.op, P.arg, t - base, sm);
         }
         if (!grid_barrier(ctl)) return;
     }
