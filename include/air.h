@@ -112,6 +112,27 @@ AIR_API air_status air_backproject(const air_plan *plan, const float *Y, float *
 AIR_API air_status air_filtered_backproject(const air_plan *plan, const float *Y, float *X,
                                     air_stream stream);
 
+/* The filtered adjoint of air_filtered_backproject for callers that cannot
+ * allocate device memory when they call it: for example code that runs under
+ * a fixed device-memory budget with no cudaMalloc after start-up, or a host
+ * thread that holds a lock which another thread's allocation would need.
+ * The paper has no counterpart; this is a deployment variant.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ *     Its one scratch buffer, the filtered sinogram, is a static device array
+ *     of 2^20 floats (4 MB) that every GPU loading the library keeps until
+ *     the process exits.
+ *   - n_views * n_bins must be <= 2^20 (1,048,576); larger plans get
+ *     AIR_ERR_INVALID_ARG.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls on a device share the array; calls that overlap on the GPU
+ *     race.  Each call writes every sample it later reads.
+ *   - Applies the FP32 filter whatever the plan's precision; Y, X as for
+ *     air_filtered_backproject, and the plan's tables are read, not its
+ *     workspace. */
+AIR_API air_status air_filtered_backproject_noalloc(const air_plan *plan, const float *Y, float *X,
+                                                    air_stream stream);
+
 /* adjoint == 0: out = W in  (in: n*n, out: 9*n*n);
  * adjoint != 0: out = W^T in (in: 9*n*n, out: n*n).  Periodic boundary;
  * W^T W = I. */

@@ -26,7 +26,8 @@ PREC_FP32, PREC_BF16X3 = 0, 1
 
 # every symbol include/air.h declares
 EXPORTS = ["air_last_error", "air_plan_create", "air_plan_destroy", "air_plan_bytes", "air_project",
-           "air_filter", "air_backproject", "air_filtered_backproject", "air_framelet", "air_shrink",
+           "air_filter", "air_backproject", "air_filtered_backproject", "air_filtered_backproject_noalloc",
+           "air_framelet", "air_shrink",
            "air_solve", "air_solve_host", "air_solve_batch", "air_server_create", "air_server_submit",
            "air_server_poll", "air_server_wait", "air_server_times", "air_server_destroy"]
 
@@ -74,6 +75,7 @@ def load(build_if_missing: bool = False):
         "air_filter": (i32, [P, P, P, P]),
         "air_backproject": (i32, [P, P, P, P]),
         "air_filtered_backproject": (i32, [P, P, P, P]),
+        "air_filtered_backproject_noalloc": (i32, [P, P, P, P]),
         "air_framelet": (i32, [P, P, P, i32, P]),
         "air_shrink": (i32, [P, P, P, P, f32, P, P]),
         "air_solve": (i32, [P, P, f32, f32, i32, i32, P, P, P]),
@@ -199,6 +201,11 @@ def air_backproject(plan: Plan, Y, X, stream=None):
 def air_filtered_backproject(plan: Plan, Y, X, stream=None):
     _check(load().air_filtered_backproject(plan.handle, _ptr(Y), _ptr(X), _stream(stream)),
            "air_filtered_backproject")
+
+
+def air_filtered_backproject_noalloc(plan: Plan, Y, X, stream=None):
+    _check(load().air_filtered_backproject_noalloc(plan.handle, _ptr(Y), _ptr(X), _stream(stream)),
+           "air_filtered_backproject_noalloc")
 
 
 def air_framelet(plan: Plan, inp, out, adjoint: bool, stream=None):

@@ -1,0 +1,80 @@
+// air_filtered_backproject_noalloc: the filtered adjoint X = A^T C Y for
+// callers that must not allocate device memory at call time -- for example
+// code running under a device-memory budget that forbids cudaMalloc after
+// start-up, or a host thread that holds a lock another thread needs to
+// allocate.  Its only scratch, the filtered sinogram C Y, lives in the
+// file-scope device array below instead of in plan or caller memory.
+#include <mutex>
+#include <string>
+
+#include "host_common.h"
+
+using namespace air;
+
+namespace {
+
+// Largest filtered sinogram the static scratch holds: n_views * n_bins.
+constexpr size_t NOALLOC_MAX_SAMPLES = size_t(1) << 20;   // 4 MB of float
+
+// Every GPU that loads this library reserves this array until the process
+// exits.  All calls on a device share it and it keeps the last call's
+// contents; every element a call reads was written earlier by the same call
+// (the filter writes all n_views * n_bins samples), so nothing needs
+// clearing.  Calls that overlap on the GPU race on it.
+static __device__ __align__(256) float g_fbp_scratch[NOALLOC_MAX_SAMPLES];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_mu;
+float *g_scratch_ptr[MAX_DEVICES] = {};
+
+// Device address of the scratch on the current device, looked up once per
+// device.  In host code g_fbp_scratch names a host-side stand-in, never a
+// device address, so kernels only ever receive the address returned here.
+air_status scratch_ptr(float **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= MAX_DEVICES) return fail(AIR_ERR_CUDA, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_fbp_scratch);
+        if (e != cudaSuccess)
+            return fail(AIR_ERR_CUDA, std::string("cudaGetSymbolAddress of the static scratch: ") +
+                                          cudaGetErrorString(e));
+        g_scratch_ptr[dev] = static_cast<float *>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return AIR_OK;
+}
+
+}  // namespace
+
+extern "C" air_status air_filtered_backproject_noalloc(const air_plan *P, const float *Y, float *X,
+                                                       air_stream stream) {
+    if (!P) return fail(AIR_ERR_INVALID_ARG, "plan is NULL");
+    const size_t samples = (size_t)P->geom.n_views * P->geom.n_bins;
+    if (samples > NOALLOC_MAX_SAMPLES)
+        return fail(AIR_ERR_INVALID_ARG, "n_views * n_bins = " + std::to_string(samples) +
+                                             " exceeds the static scratch of this call (" +
+                                             std::to_string(NOALLOC_MAX_SAMPLES) + " samples)");
+    air_status st = check_dev_ptr(Y, "Y");
+    if (st != AIR_OK) return st;
+    if ((st = check_dev_ptr(X, "X")) != AIR_OK) return st;
+    if (overlap(X, (size_t)P->geom.n * P->geom.n * 4, Y, samples * 4))
+        return fail(AIR_ERR_INVALID_ARG, "X and Y overlap");
+    float *scratch = nullptr;
+    if ((st = scratch_ptr(&scratch)) != AIR_OK) return st;
+    const cudaStream_t s = (cudaStream_t)stream;
+    SliceDesc d = P->desc;
+    d.ext_in = Y;            // C Y into the static scratch (FP32 filter)
+    d.ext_out = scratch;
+    cudaError_t e = launch_op(OP_RAMP, d, RSRC_EXT, s);
+    if (e == cudaSuccess) {
+        d.ext_in = scratch;  // X = A^T (C Y)
+        d.ext_out = X;
+        e = launch_op(OP_BWD, d, BWD_PLAIN, s);
+    }
+    if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("filtered backprojection: ") + cudaGetErrorString(e));
+    return AIR_OK;
+}
