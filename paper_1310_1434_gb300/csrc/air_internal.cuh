@@ -34,6 +34,7 @@ enum Op : int {
     OP_FRAMELET,   // out = W in            (API call)
     OP_FRAMELET_T, // out = W^T in          (API call)
     OP_TRANSPOSE,  // xt = transpose(src)   (before every OP_FWD; arg = FwdSrc)
+    OP_BWD_FIN,    // sum the backprojector's view parts, then the BwdMode epilogue
     OP_COUNT
 };
 
@@ -94,6 +95,8 @@ struct SliceDesc {
     // solver state (plan-owned workspace)
     float *x, *r, *p, *q, *rhs0, *g;   // n*n
     float *xt;                         // n*n: transposed copy of the projector's input
+    float *bwd_part;                   // bwd_parts * n*n: the backprojector's per-view-part sums
+    int bwd_parts;                     // S: views split over S blocks per pixel tile
     float *b, *b2;                     // 9*n*n each (Bregman variable, double-buffered)
     float *z, *zc;                     // V*nb
     const float *y;                    // V*nb measured sinogram
@@ -120,11 +123,13 @@ __host__ __device__ inline int tiles_fwd(const SliceDesc &s) {
     return (s.V * s.nb + AIR_THREADS - 1) / AIR_THREADS;
 }
 __host__ __device__ inline int tiles_ramp(const SliceDesc &s) { return s.V; }
-// backprojector tile: 8 x 8 pixels, the views split over 4 interleaved groups
-constexpr int BWD_TX = 8, BWD_TY = 8, BWD_GROUPS = AIR_THREADS / (BWD_TX * BWD_TY);
-__host__ __device__ inline int tiles_bwd(const SliceDesc &s) {
-    return ((s.n + BWD_TX - 1) / BWD_TX) * ((s.n + BWD_TY - 1) / BWD_TY);
+// backprojector tile: 16 x 16 pixels x one of bwd_parts view parts; the
+// block's 256 threads are 16 view slots x 16 strip lanes
+constexpr int BWD_T = 16, BWD_SLOTS = AIR_THREADS / BWD_T, BWD_PAD = BWD_T + 1;
+__host__ __device__ inline int tiles_bwd_xy(const SliceDesc &s) {
+    return ((s.n + BWD_T - 1) / BWD_T) * ((s.n + BWD_T - 1) / BWD_T);
 }
+__host__ __device__ inline int tiles_bwd(const SliceDesc &s) { return tiles_bwd_xy(s) * s.bwd_parts; }
 constexpr int VEC_PER_TILE = AIR_THREADS * 4;   // elementwise ops: 4 per thread
 __host__ __device__ inline int tiles_vec(const SliceDesc &s) {
     return (s.n * s.n + VEC_PER_TILE - 1) / VEC_PER_TILE;
@@ -138,15 +143,15 @@ __host__ __device__ inline int tiles_of(const SliceDesc &s, int op) {
     case OP_FWD: return tiles_fwd(s);
     case OP_RAMP: return tiles_ramp(s);
     case OP_BWD: return tiles_bwd(s);
-    case OP_CG_A: case OP_CG_B: case OP_ZERO: return tiles_vec(s);
+    case OP_CG_A: case OP_CG_B: case OP_ZERO: case OP_BWD_FIN: return tiles_vec(s);
     case OP_SHRINK: case OP_FRAMELET: case OP_FRAMELET_T: case OP_TRANSPOSE: return tiles_shr(s);
     default: return 0;
     }
 }
 // largest number of tiles of any reducing op: sizes SliceDesc::partial
 __host__ inline int max_reduce_tiles(const SliceDesc &s) {
-    int a = tiles_bwd(s), b = tiles_vec(s), c = tiles_shr(s);
-    return a > b ? (a > c ? a : c) : (b > c ? b : c);
+    const int b = tiles_vec(s), c = tiles_shr(s);
+    return b > c ? b : c;
 }
 
 // ------------------------------------------------ block reductions -------

@@ -57,7 +57,7 @@ extern "C" air_status air_solve_batch(int n, air_plan *const *plans, const float
         slices[i] = solve_desc(plans[i], Y[i], lambda[i], mu[i], X[i], nullptr);
         progs[i] = solve_program(n_outer[i], n_cg[i], false);
         nphases = std::max(nphases, progs[i].size());
-        for (int op : {OP_RAMP, OP_SHRINK, OP_TRANSPOSE}) smem = std::max(smem, tile_smem(slices[i], op));
+        for (int op : {OP_RAMP, OP_SHRINK, OP_TRANSPOSE, OP_BWD}) smem = std::max(smem, tile_smem(slices[i], op));
     }
     std::vector<Phase> prog(n * nphases, Phase{OP_NOP, 0});
     for (int i = 0; i < n; ++i) std::memcpy(&prog[i * nphases], progs[i].data(), progs[i].size() * sizeof(Phase));

@@ -146,9 +146,24 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     s.jmid = 0.5f * (nb - 1);
     s.filter = g.filter;
 
+    // backprojector view parts: enough (pixel tile, part) blocks for ~4
+    // waves of 6 resident blocks per SM, at most one part per view
+    int sms = 148;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaGetLastError();
+    }
+    s.bwd_parts = 1;
+    {
+        const int txy = tiles_bwd_xy(s), target = 4 * 6 * sms;
+        int S = (target + txy - 1) / txy;
+        s.bwd_parts = S < 1 ? 1 : (S > V ? V : S);
+    }
     // carve one allocation
     struct Piece { void **dst; size_t bytes; };
-    float *x, *r, *p, *q, *rhs0, *gg, *b, *b2, *z, *zc, *ybuf, *xbuf, *xt;
+    float *x, *r, *p, *q, *rhs0, *gg, *b, *b2, *z, *zc, *ybuf, *xbuf, *xt, *bpart;
     RayFx *ray;
     float4 *view;
     float *taps;
@@ -157,7 +172,7 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     const size_t npart = (size_t)max_reduce_tiles(s) + 64;
     std::vector<Piece> pieces = {
         {(void **)&ray, rays * sizeof(RayFx)}, {(void **)&view, (size_t)V * sizeof(float4)},
-        {(void **)&xt, nn * 4},
+        {(void **)&xt, nn * 4}, {(void **)&bpart, (size_t)s.bwd_parts * nn * 4},
         {(void **)&taps, (size_t)nb * sizeof(float)},
         {(void **)&x, nn * 4}, {(void **)&r, nn * 4}, {(void **)&p, nn * 4}, {(void **)&q, nn * 4},
         {(void **)&rhs0, nn * 4}, {(void **)&gg, nn * 4}, {(void **)&b, 9 * nn * 4}, {(void **)&b2, 9 * nn * 4},
@@ -222,6 +237,7 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     s.view = view;
     s.taps = taps;
     s.x = x; s.r = r; s.p = p; s.q = q; s.rhs0 = rhs0; s.g = gg; s.b = b; s.b2 = b2; s.xt = xt;
+    s.bwd_part = bpart;
     s.z = z; s.zc = zc; s.y = ybuf;
     s.cg = cg;
     s.partial = partial;
@@ -331,6 +347,7 @@ extern "C" air_status air_backproject(const air_plan *P, const float *Y, float *
     s.ext_in = Y;
     s.ext_out = X;
     CUDA_TRY(launch_op(OP_BWD, s, BWD_PLAIN, (cudaStream_t)stream));
+    if (s.bwd_parts > 1) CUDA_TRY(launch_op(OP_BWD_FIN, s, BWD_PLAIN, (cudaStream_t)stream));
     return AIR_OK;
 }
 
@@ -346,6 +363,7 @@ extern "C" air_status air_filtered_backproject(const air_plan *P, const float *Y
     s.ext_in = P->desc.zc;
     s.ext_out = X;
     CUDA_TRY(launch_op(OP_BWD, s, BWD_PLAIN, st));
+    if (s.bwd_parts > 1) CUDA_TRY(launch_op(OP_BWD_FIN, s, BWD_PLAIN, st));
     return AIR_OK;
 }
 
@@ -397,17 +415,20 @@ std::vector<Phase> solve_program(int n_outer, int n_cg, bool tc_ramp) {
     const int ramp = tc_ramp ? OP_RAMP_TC : OP_RAMP;
     prog.push_back({ramp, RSRC_Y});        // zc = C y
     prog.push_back({OP_BWD, BWD_RHS0});   // rhs0 = A^T zc
+    prog.push_back({OP_BWD_FIN, BWD_RHS0});
     prog.push_back({OP_ZERO, 0});         // X = 0, b = 0, g = 0
     for (int k = 0; k < n_outer; ++k) {
         prog.push_back({OP_TRANSPOSE, SRC_X});        // r = rhs0 + mu g - M x, p = r
         prog.push_back({OP_FWD, SRC_X});
         prog.push_back({ramp, RSRC_Z});
         prog.push_back({OP_BWD, BWD_RESID});
+        prog.push_back({OP_BWD_FIN, BWD_RESID});
         for (int i = 0; i < n_cg; ++i) {
             prog.push_back({OP_TRANSPOSE, SRC_P});    // q = M p
             prog.push_back({OP_FWD, SRC_P});
             prog.push_back({ramp, RSRC_Z});
             prog.push_back({OP_BWD, BWD_Q});
+            prog.push_back({OP_BWD_FIN, BWD_Q});
             prog.push_back({OP_CG_A, 0});
             prog.push_back({OP_CG_B, 0});
         }

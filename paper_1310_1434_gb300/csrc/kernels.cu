@@ -17,7 +17,9 @@ __global__ void __launch_bounds__(AIR_THREADS) k_op(const SliceDesc s, int arg) 
     } else if constexpr (OP == OP_RAMP) {
         tile_ramp(s, arg, tile, sm);
     } else if constexpr (OP == OP_BWD) {
-        tile_bwd(s, arg, tile);
+        tile_bwd(s, arg, tile, sm);
+    } else if constexpr (OP == OP_BWD_FIN) {
+        tile_bwd_fin(s, arg, tile);
     } else if constexpr (OP == OP_CG_A) {
         tile_cg_a(s, tile);
     } else if constexpr (OP == OP_CG_B) {
@@ -67,6 +69,7 @@ cudaError_t launch_op(int op, const SliceDesc &s, int arg, cudaStream_t st) {
     case OP_FRAMELET: return launch_one<OP_FRAMELET>(s, 0, st);
     case OP_FRAMELET_T: return launch_one<OP_FRAMELET>(s, 1, st);
     case OP_TRANSPOSE: return launch_one<OP_TRANSPOSE>(s, arg, st);
+    case OP_BWD_FIN: return launch_one<OP_BWD_FIN>(s, arg, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -71,8 +71,10 @@ extern "C" air_status air_filtered_backproject_noalloc(const air_plan *P, const 
     d.ext_out = scratch;
     cudaError_t e = launch_op(OP_RAMP, d, RSRC_EXT, s);
     if (e == cudaSuccess) {
-        d.ext_in = scratch;  // X = A^T (C Y)
+        d.ext_in = scratch;  // X = A^T (C Y), in one view part: written straight to X
         d.ext_out = X;
+        d.bwd_parts = 1;
+        d.bwd_part = nullptr;
         e = launch_op(OP_BWD, d, BWD_PLAIN, s);
     }
     if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("filtered backprojection: ") + cudaGetErrorString(e));

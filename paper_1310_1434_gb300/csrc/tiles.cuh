@@ -16,8 +16,8 @@ namespace air {
 // walking columns reads the transposed image so that the 32 neighbouring
 // rays of a warp read neighbouring addresses.
 // ======================================================================
-__device__ __forceinline__ float fx_len(unsigned long long ov, float c) {
-    return __fmul_rn(__ull2float_rn(ov), c);
+__device__ __forceinline__ float fx_len(unsigned ov, float c) {
+    return __fmul_rn(__uint2float_rn(ov), c);
 }
 
 __device__ __forceinline__ float fx_ray(const float *__restrict__ X, const float *__restrict__ XT, int n,
@@ -73,67 +73,6 @@ __device__ __forceinline__ void tile_transpose(const SliceDesc &s, int arg, int 
     __syncthreads();
 }
 
-// ======================================================================
-// Backprojector A^T: gather per pixel over every view and every bin whose
-// ray meets the pixel.  The bins are found from the fan angle of the pixel
-// centre widened by the pixel's angular half-width and a margin; each
-// candidate's length is the exact integer overlap of its fixed-point span
-// with the pixel, the same number tile_fwd uses, so the sum is the exact
-// transpose of the projector without atomics.
-// ======================================================================
-// arctan(u) for |u| <= 0.45 by its Maclaurin (Gregory) series through u^13;
-// the alternating-series remainder is below 0.45^15/15 = 4.2e-7 rad, far
-// inside the margin of the bin search below.
-__device__ __forceinline__ float atan_series(float u) {
-    const float w = u * u;
-    float p = 1.f / 13.f;
-    p = fmaf(p, w, -1.f / 11.f);
-    p = fmaf(p, w, 1.f / 9.f);
-    p = fmaf(p, w, -1.f / 7.f);
-    p = fmaf(p, w, 1.f / 5.f);
-    p = fmaf(p, w, -1.f / 3.f);
-    p = fmaf(p, w, 1.f);
-    return u * p;
-}
-
-// Sum over views v0, v0 + dv, ... of pixel (ix, iy)'s backprojection.
-__device__ __forceinline__ float bwd_pixel(const SliceDesc &s, const float *__restrict__ Z, int ix, int iy,
-                                           int v0, int dv) {
-    const float xc = (float)ix + 0.5f - s.half_n, yc = (float)iy + 0.5f - s.half_n;
-    const int nb = s.nb;
-    float acc = 0.f;
-#pragma unroll 1
-    for (int v = v0; v < s.V; v += dv) {
-        const float4 w = __ldg(s.view + v);
-        const float dxs = xc - w.x, dys = yc - w.y;
-        const float cr = w.z * dys - w.w * dxs;   // L sin(gamma): c x d
-        const float dt = w.z * dxs + w.w * dys;   // L cos(gamma): c . d  (> 0)
-        const float u = __fdividef(cr, dt);
-        const float gam = fabsf(u) <= 0.45f ? atan_series(u) : atan2f(cr, dt);
-        // half-width of the pixel's fan-angle footprint: sin(phi) <=
-        // (|dx|+|dy|)/2 / (L (L - 0.75)) <= (|dx|+|dy|)/2 / L^2 * half_k, with
-        // half_k = 1.002 / (1 - 0.75/L_min) covering asin and L >= L_min
-        const float half = 0.5f * (fabsf(dxs) + fabsf(dys)) * __fdividef(s.half_k, fmaf(dxs, dxs, dys * dys));
-        const float jc = fmaf(gam, s.inv_dgamma, s.jmid);
-        const float hw = fmaf(half, s.inv_dgamma, 0.02f);
-        const int jlo = max(0, (int)ceilf(jc - hw));
-        const int jhi = min(nb - 1, (int)floorf(jc + hw));
-        const RayFx *rr = s.ray + (size_t)v * nb;
-        const float *zz = Z + (size_t)v * nb;
-        for (int j = jlo; j <= jhi; ++j) {
-            const RayFx r = rr[j];
-            const int k = r.o ? ix : iy, rw = r.o ? iy : ix;
-            const long long lo = r.L0 + (long long)k * r.M;
-            const long long hi = lo + (long long)r.Ma;
-            const long long rb = (long long)rw << 32;
-            const long long a = lo > rb ? lo : rb;
-            const long long b = hi < rb + (1ll << 32) ? hi : rb + (1ll << 32);
-            if (b > a) acc = fmaf(fx_len((unsigned long long)(b - a), r.c), __ldg(zz + j), acc);
-        }
-    }
-    return acc;
-}
-
 // Sum `val` (valid in thread 0) of this tile into the slice's partials; the
 // tile that completes the phase sums all partials in a fixed order and gets
 // true with the total in *total (thread 0 only).
@@ -159,56 +98,147 @@ __device__ __forceinline__ bool reduce_tiles(const SliceDesc &s, int tile, int n
     return true;
 }
 
-__device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile) {
-    __shared__ double sh[AIR_THREADS / 32];
-    __shared__ float red[BWD_GROUPS][BWD_TX * BWD_TY];
+// ======================================================================
+// Backprojector A^T, the exact transpose of tile_fwd, without atomics.
+// A tile is a 16 x 16 block of pixels and one of S parts of the views.  The
+// block's threads are 16 view slots of 16 lanes: for each of its views a slot
+// sweeps every ray that can meet the tile, and lane c takes the tile's column
+// c for rays that walk columns and its row c for rays that walk rows.  There
+// the ray's span touches one or two pixels of the lane's strip, with the same
+// integer overlaps the projector computes, and the lane adds length * Z to
+// its own shared-memory accumulator of that pixel.  Each pixel's sum is
+// thereby formed in a fixed order by one lane per slot; the slots are then
+// summed in a fixed order, and the S parts by OP_BWD_FIN.
+// ======================================================================
+// arctan(u) for |u| <= 0.45 by its Maclaurin (Gregory) series through u^13;
+// the alternating-series remainder is below 0.45^15/15 = 4.2e-7 rad, far
+// inside the margin of the bin search below.
+__device__ __forceinline__ float atan_series(float u) {
+    const float w = u * u;
+    float p = 1.f / 13.f;
+    p = fmaf(p, w, -1.f / 11.f);
+    p = fmaf(p, w, 1.f / 9.f);
+    p = fmaf(p, w, -1.f / 7.f);
+    p = fmaf(p, w, 1.f / 5.f);
+    p = fmaf(p, w, -1.f / 3.f);
+    p = fmaf(p, w, 1.f);
+    return u * p;
+}
+
+// Fan angle of point (x, y) (pixel units, centred) seen from the source of
+// view w = {sx, sy, cx, cy}, measured from the central ray.
+__device__ __forceinline__ float fan_angle(float4 w, float x, float y) {
+    const float dxs = x - w.x, dys = y - w.y;
+    const float cr = w.z * dys - w.w * dxs;   // L sin(gamma)
+    const float dt = w.z * dxs + w.w * dys;   // L cos(gamma), > 0
+    const float u = __fdividef(cr, dt);
+    return fabsf(u) <= 0.45f ? atan_series(u) : atan2f(cr, dt);
+}
+
+// Shared memory of a backprojector tile: two [slots][lanes][16 + 1] arrays.
+constexpr int BWD_SMEM_FLOATS = 2 * BWD_SLOTS * BWD_T * BWD_PAD;
+
+__device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile, float *sm) {
     if (mode == BWD_Q && s.cg->stop) return;
-    const int tx = (s.n + BWD_TX - 1) / BWD_TX;
-    const int pix = threadIdx.x % (BWD_TX * BWD_TY), grp = threadIdx.x / (BWD_TX * BWD_TY);
-    const int ix = (tile % tx) * BWD_TX + pix % BWD_TX;
-    const int iy = (tile / tx) * BWD_TY + pix / BWD_TX;
-    const bool inside = ix < s.n && iy < s.n;
-    const float *Z = mode == BWD_PLAIN ? s.ext_in : s.zc;
-    red[grp][pix] = inside ? bwd_pixel(s, Z, ix, iy, grp, BWD_GROUPS) : 0.f;
+    const int n = s.n, nb = s.nb;
+    const int ntxy = tiles_bwd_xy(s), part = tile / ntxy, txy = tile - part * ntxy;
+    const int tpr = (n + BWD_T - 1) / BWD_T;
+    const int X0 = (txy % tpr) * BWD_T, Y0 = (txy / tpr) * BWD_T;
+    float *accH = sm;                                  // [slot][column lane][row]
+    float *accV = sm + BWD_SLOTS * BWD_T * BWD_PAD;    // [slot][row lane][column]
+    for (int i = threadIdx.x; i < BWD_SMEM_FLOATS; i += AIR_THREADS) sm[i] = 0.f;
     __syncthreads();
-    // view groups summed in a fixed order; the epilogue runs on group 0
-    const bool in = inside && grp == 0;
+    const int q = threadIdx.x / BWD_T, c = threadIdx.x % BWD_T;
+    const float *__restrict__ Z = mode == BWD_PLAIN ? s.ext_in : s.zc;
+    float *aH = accH + (q * BWD_T + c) * BWD_PAD;
+    float *aV = accV + (q * BWD_T + c) * BWD_PAD;
+    const int colk = X0 + c, rowk = Y0 + c;
+    const int nvH = min(BWD_T, n - Y0), nvV = min(BWD_T, n - X0);
+    // tile corners, pixel units, centred
+    const float xa = (float)X0 - s.half_n, xb = (float)min(X0 + BWD_T, n) - s.half_n;
+    const float ya = (float)Y0 - s.half_n, yb = (float)min(Y0 + BWD_T, n) - s.half_n;
+    const int S = s.bwd_parts;
+#pragma unroll 1
+    for (int v = part + S * q; v < s.V; v += S * BWD_SLOTS) {
+        const float4 w = __ldg(s.view + v);
+        const float g0 = fan_angle(w, xa, ya), g1 = fan_angle(w, xb, ya);
+        const float g2 = fan_angle(w, xa, yb), g3 = fan_angle(w, xb, yb);
+        const float gmin = fminf(fminf(g0, g1), fminf(g2, g3)), gmax = fmaxf(fmaxf(g0, g1), fmaxf(g2, g3));
+        const int J0 = max(0, (int)ceilf(fmaf(gmin, s.inv_dgamma, s.jmid) - 0.02f));
+        const int J1 = min(nb - 1, (int)floorf(fmaf(gmax, s.inv_dgamma, s.jmid) + 0.02f));
+        const RayFx *__restrict__ rr = s.ray + (size_t)v * nb;
+        const float *__restrict__ zz = Z + (size_t)v * nb;
+#pragma unroll 2
+        for (int j = J0; j <= J1; ++j) {
+            const RayFx r = rr[j];
+            const float z = __ldg(zz + j);
+            const int k = r.o ? colk : rowk;
+            const int base = r.o ? Y0 : X0;
+            const int nv = r.o ? nvH : nvV;
+            float *a = r.o ? aH : aV;
+            const long long lo = r.L0 + (long long)k * r.M;
+            const long long hi = lo + (long long)r.Ma;
+            const int r0 = (int)(lo >> 32);
+            const int r1 = (int)((hi - 1) >> 32);
+            const bool two = r1 != r0;
+            const unsigned ov0 = two ? 0u - (unsigned)lo : r.Ma;
+            const unsigned ov1 = two ? (unsigned)hi : 0u;
+            const int i0 = r0 - base, i1 = r1 - base;
+            if (k < n && (unsigned)i0 < (unsigned)nv) a[i0] = fmaf(fx_len(ov0, r.c), z, a[i0]);
+            if (k < n && two && (unsigned)i1 < (unsigned)nv) a[i1] = fmaf(fx_len(ov1, r.c), z, a[i1]);
+        }
+    }
+    __syncthreads();
+    const int lx = threadIdx.x % BWD_T, ly = threadIdx.x / BWD_T;
     float acc = 0.f;
-    if (in) {
-#pragma unroll
-        for (int k = 0; k < BWD_GROUPS; ++k) acc += red[k][pix];
-        acc *= s.dx;
+#pragma unroll 4
+    for (int k = 0; k < BWD_SLOTS; ++k)
+        acc += accH[(k * BWD_T + lx) * BWD_PAD + ly] + accV[(k * BWD_T + ly) * BWD_PAD + lx];
+    const int ix = X0 + lx, iy = Y0 + ly;
+    if (ix < n && iy < n) {
+        if (S == 1 && mode == BWD_PLAIN) s.ext_out[iy * n + ix] = s.dx * acc;
+        else s.bwd_part[(size_t)part * n * n + iy * n + ix] = acc;
     }
-    __syncthreads();   // red is reused by the next tile of a persistent block
-    const int i = iy * s.n + ix;
-    if (mode == BWD_PLAIN) {
-        if (in) s.ext_out[i] = acc;
-        return;
-    }
-    if (mode == BWD_RHS0) {
-        if (in) s.rhs0[i] = acc;
-        return;
-    }
+    __syncthreads();   // shared memory is reused by the next tile of a persistent block
+}
+
+
+// Sums the S view parts of the backprojection in a fixed order and applies
+// the mode's epilogue (the CG and residual updates of the Eq. 5 system).
+__device__ __forceinline__ void tile_bwd_fin(const SliceDesc &s, int mode, int tile) {
+    __shared__ double sh[AIR_THREADS / 32];
+    if (mode == BWD_Q && s.cg->stop) return;
+    const int nn = s.n * s.n, S = s.bwd_parts;
+    const int base = tile * VEC_PER_TILE;
     double part = 0.0;
-    if (mode == BWD_RESID) {
-        if (in) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = base + k * AIR_THREADS + threadIdx.x;
+        if (i >= nn) continue;
+        float a = 0.f;
+        for (int p = 0; p < S; ++p) a += __ldcg(s.bwd_part + (size_t)p * nn + i);
+        const float acc = s.dx * a;
+        if (mode == BWD_PLAIN) {
+            s.ext_out[i] = acc;
+        } else if (mode == BWD_RHS0) {
+            s.rhs0[i] = acc;
+        } else if (mode == BWD_RESID) {
             const float mx = fmaf(s.mu, s.x[i], acc);
             const float rv = fmaf(s.mu, s.g[i], s.rhs0[i]) - mx;
             s.r[i] = rv;
             s.p[i] = rv;
-            part = (double)rv * (double)rv;
-        }
-    } else {  // BWD_Q
-        if (in) {
+            part += (double)rv * (double)rv;
+        } else {  // BWD_Q
             const float pv = s.p[i];
             const float qv = fmaf(s.mu, pv, acc);
             s.q[i] = qv;
-            part = (double)pv * (double)qv;
+            part += (double)pv * (double)qv;
         }
     }
+    if (mode == BWD_PLAIN || mode == BWD_RHS0) return;
     part = block_sum(part, sh);
     double tot;
-    if (reduce_tiles(s, tile, tiles_bwd(s), part, sh, &tot) && threadIdx.x == 0) {
+    if (reduce_tiles(s, tile, tiles_vec(s), part, sh, &tot) && threadIdx.x == 0) {
         CgState *c = s.cg;
         if (mode == BWD_RESID) {
             c->rho = tot;
@@ -551,6 +581,7 @@ __host__ inline size_t tile_smem(const SliceDesc &s, int op) {
     case OP_SHRINK: return sizeof(float) * SHR_SMEM_FLOATS;
     case OP_FRAMELET: case OP_FRAMELET_T: return sizeof(float) * 9 * SHR_H * SHR_H;
     case OP_TRANSPOSE: return sizeof(float) * 32 * 33;
+    case OP_BWD: return sizeof(float) * BWD_SMEM_FLOATS;
     default: return 0;
     }
 }
@@ -561,7 +592,8 @@ __device__ __forceinline__ void run_tile(const SliceDesc &s, int op, int arg, in
     case OP_FWD: tile_fwd(s, arg, tile); break;
     case OP_TRANSPOSE: tile_transpose(s, arg, tile, sm); break;
     case OP_RAMP: tile_ramp(s, arg, tile, sm); break;
-    case OP_BWD: tile_bwd(s, arg, tile); break;
+    case OP_BWD: tile_bwd(s, arg, tile, sm); break;
+    case OP_BWD_FIN: tile_bwd_fin(s, arg, tile); break;
     case OP_CG_A: tile_cg_a(s, tile); break;
     case OP_CG_B: tile_cg_b(s, tile); break;
     case OP_ZERO: tile_zero(s, tile); break;
