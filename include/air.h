@@ -89,6 +89,11 @@ AIR_API const char *air_last_error(void);
  * owns all of it; free with air_plan_destroy.  Synchronous. */
 AIR_API air_status air_plan_create(const air_geometry *geom, air_plan **out);
 AIR_API air_status air_plan_destroy(air_plan *plan);
+/* Status recorded on the device by the plan's kernels: AIR_OK, or
+ * AIR_ERR_TIMEOUT if a bounded wait inside a kernel gave up (the kernel then
+ * returned without its result).  Synchronises the device.  The status word is
+ * cleared by air_plan_create only. */
+AIR_API air_status air_plan_status(const air_plan *plan);
 /* Device bytes the plan holds (tables + workspace). */
 AIR_API size_t     air_plan_bytes(const air_plan *plan);
 

@@ -25,7 +25,8 @@ FILTER_NONE, FILTER_RAMLAK = 0, 1
 PREC_FP32, PREC_BF16X3 = 0, 1
 
 # every symbol include/air.h declares
-EXPORTS = ["air_last_error", "air_plan_create", "air_plan_destroy", "air_plan_bytes", "air_project",
+EXPORTS = ["air_last_error", "air_plan_create", "air_plan_destroy", "air_plan_bytes", "air_plan_status",
+           "air_project",
            "air_filter", "air_backproject", "air_filtered_backproject", "air_filtered_backproject_noalloc",
            "air_framelet", "air_shrink",
            "air_solve", "air_solve_host", "air_solve_batch", "air_server_create", "air_server_submit",
@@ -71,6 +72,7 @@ def load(build_if_missing: bool = False):
         "air_plan_create": (i32, [g, ctypes.POINTER(P)]),
         "air_plan_destroy": (i32, [P]),
         "air_plan_bytes": (ctypes.c_size_t, [P]),
+        "air_plan_status": (i32, [P]),
         "air_project": (i32, [P, P, P, P]),
         "air_filter": (i32, [P, P, P, P]),
         "air_backproject": (i32, [P, P, P, P]),
@@ -184,6 +186,10 @@ def air_plan_create(geom) -> Plan:
 
 def air_plan_destroy(plan: Plan):
     plan.close()
+
+
+def air_plan_status(plan: Plan):
+    _check(load().air_plan_status(plan.handle), "air_plan_status")
 
 
 def air_project(plan: Plan, X, Y, stream=None):

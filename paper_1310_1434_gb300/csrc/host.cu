@@ -288,6 +288,14 @@ extern "C" air_status air_plan_destroy(air_plan *P) {
 
 extern "C" size_t air_plan_bytes(const air_plan *P) { return P ? P->bytes + P->tc_bytes : 0; }
 
+extern "C" air_status air_plan_status(const air_plan *P) {
+    if (!P) return fail(AIR_ERR_INVALID_ARG, "plan is NULL");
+    const int st = ramp_tc_status(P);
+    if (st == (int)AIR_ERR_TIMEOUT) return fail(AIR_ERR_TIMEOUT, "a bounded wait in the tensor-core filter gave up");
+    if (st != 0) return fail(AIR_ERR_CUDA, "reading the plan status failed");
+    return AIR_OK;
+}
+
 // ------------------------------------------------------- stand-alone ops
 #define TRY(expr)                                   \
     do {                                            \
@@ -496,5 +504,5 @@ extern "C" air_status air_solve_host(const air_plan *P, const float *Y_host, flo
     TRY(run_program_single(P, s, solve_program(n_outer, n_cg, tc), st));
     CUDA_TRY(cudaMemcpyAsync(X_host, P->xbuf, img_bytes(P), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
-    return AIR_OK;
+    return tc ? air_plan_status(P) : AIR_OK;
 }

@@ -11,4 +11,7 @@ void ramp_tc_destroy(air_plan *P);
 // cg->stop is set (the CG of this outer step has ended).
 air_status ramp_tc_apply(const air_plan *P, const float *src, float *dst, const CgState *cg,
                          int respect_stop, cudaStream_t st);
+// The plan's tensor-core status word (0, or AIR_ERR_TIMEOUT after a bounded
+// wait gave up); synchronous.
+int ramp_tc_status(const air_plan *P);
 }  // namespace air
