@@ -20,6 +20,7 @@ time over ranks.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import subprocess
@@ -167,30 +168,45 @@ def events_time(torch, stream, fn, reps: int) -> float:
     return a.elapsed_time(b) / reps
 
 
-def cpu_baseline(sample_cg_steps: int = 2):
-    """The FP64 oracle (as it stands) on this host: a bounded sample of one
-    800-view 512^2 slice -- A'^T Y once and sample_cg_steps CG steps -- scaled
-    to one full 30 x (8 + 1) operator-pair solve.  Returns slices/s."""
+def cpu_baseline(gpu):
+    """The FP64 oracle (as it stands) on this host's cores, on a bounded
+    sample of the workload: one A and one A'^T application and one shrink of
+    the 512^2/800-view slice, scaled to a full solve (A'^T Y once, then
+    30 x (8 + 1) operator pairs and 30 shrinks).  The same oracle outputs give
+    the GPU's single-application errors, and the stored oracle reconstructions
+    (tests/golden, written by the oracle) the final-image errors."""
     import oracle
+    oracle.build()
     w = inputs.AIR512_V800
     og = oracle.Geometry(**{k: getattr(w.geom, k) for k in oracle.Geometry.__dataclass_fields__})
-    _, _, Y = inputs.make_case(w)
+    ell, _, Y = inputs.make_case(w)
+    Y = Y.astype(np.float32).astype(np.float64)
+    X = inputs.rasterize(w.geom, ell).astype(np.float32).astype(np.float64)
     t = time.perf_counter()
-    rhs = oracle.filtered_backproject(og, Y)
-    t_rhs = time.perf_counter() - t
+    A_o = oracle.project(og, X)
+    t_a = time.perf_counter() - t
     t = time.perf_counter()
-    oracle.cg(og, rhs, w.mu, sample_cg_steps)   # 1 residual + sample_cg_steps operator pairs
-    t_cg = time.perf_counter() - t
-    t_pair = t_cg / (sample_cg_steps + 1)
+    ATC_o = oracle.filtered_backproject(og, Y)
+    t_atc = time.perf_counter() - t
     t = time.perf_counter()
-    oracle.shrink(np.zeros((w.geom.n, w.geom.n)), np.zeros((9, w.geom.n, w.geom.n)), w.lam / w.mu)
+    oracle.shrink(X, np.zeros((9, w.geom.n, w.geom.n)), w.lam / w.mu)
     t_shr = time.perf_counter() - t
-    t_solve = t_rhs + w.n_outer * ((w.n_cg + 1) * t_pair + t_shr)
+    t_solve = t_atc + w.n_outer * ((w.n_cg + 1) * (t_a + t_atc) + t_shr)
+
+    def rel(a, b):
+        return float(np.linalg.norm(np.asarray(a, np.float64).ravel() - b.ravel()) / np.linalg.norm(b))
+
+    prec = {"A_fp32": rel(gpu["A"], A_o), "ATC_fp32": rel(gpu["ATC_fp32"], ATC_o),
+            "ATC_bf16x3": rel(gpu["ATC_bf16x3"], ATC_o)}
+    for key, name in (("X_v800", "air512_v800"), ("X_v200", "air512_v200")):
+        path = os.path.join(ROOT, "tests", "golden", f"{name}_oracle.npz")
+        if key in gpu and os.path.exists(path):
+            prec[f"final_{name}_bf16x3_batched"] = rel(gpu[key], np.load(path)["X"].astype(np.float64))
     return {"value": 1.0 / t_solve, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": (f"FP64 oracle, one 512^2/800-view slice: A'^T Y once, {sample_cg_steps} CG steps "
-                       f"(+ residual) and one shrink, {t_rhs + t_cg + t_shr:.1f} s, scaled to "
-                       f"{w.n_outer} x ({w.n_cg}+1) operator pairs + {w.n_outer} shrinks per slice"),
-            "seconds_per_slice": t_solve}
+            "sample": (f"FP64 oracle on one 512^2/800-view slice: one A ({t_a:.2f} s), one A'^T ({t_atc:.2f} s) "
+                       f"and one shrink ({t_shr:.2f} s), scaled to A'^T Y once + {w.n_outer} x ({w.n_cg}+1) "
+                       f"operator pairs + {w.n_outer} shrinks per slice"),
+            "seconds_per_slice": t_solve}, prec
 
 
 def run_reference(args, rank, world):
@@ -255,7 +271,9 @@ def main():
     Yh = [inputs.make_case(w)[2].astype(np.float32).ravel() for w in ws]
     Yd = [torch.as_tensor(y, device=dev) for y in Yh]
     Xd = [torch.empty(w.geom.n ** 2, device=dev) for w in ws]
-    plans = [air.Plan(w.geom) for w in ws]
+    # the served/batched mixed-precision form: split-BF16 tensor-core filter
+    plans = [air.Plan(dataclasses.replace(w.geom, precision=1)) for w in ws]
+    plans32 = [air.Plan(w.geom) for w in ws]
     lam = [w.lam for w in ws]
     mu = [w.mu for w in ws]
     no = [w.n_outer for w in ws]
@@ -264,6 +282,12 @@ def main():
 
     def step():
         air.air_solve_batch(plans, Yd, lam, mu, no, ncg, Xd)
+
+    # kernels per step: one grouped launch per phase of the common program,
+    # plus two tensor-core filter kernels per slice per filter phase
+    n_ph_outer = 5 + 7 * ws[0].n_cg + 1
+    n_filter = 1 + ws[0].n_outer * (1 + ws[0].n_cg)
+    launches_per_step = (4 + ws[0].n_outer * n_ph_outer - n_filter) + 2 * B * n_filter
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -290,6 +314,8 @@ def main():
         dist.barrier()
     total_ms = float(sum(ms))
 
+    final_images = {"X_v800": Xd[0].cpu().numpy(), "X_v200": Xd[1].cpu().numpy()}
+
     # ---- e2e: pinned host buffers in and out inside the timed region ----
     Yp = [torch.from_numpy(y).pin_memory() for y in Yh]
     Xp = [torch.empty(w.geom.n ** 2, pin_memory=True) for w in ws]
@@ -309,19 +335,35 @@ def main():
     h2d = sum(y.nbytes for y in Yh)
     d2h = sum(x.numel() * 4 for x in Xp)
 
+    # ---- the other forms on the same batch (device-resident, L2 flushed) ----
+    def form_rate(fn, reps=2):
+        fn()
+        t = []
+        for _ in range(reps):
+            flush.zero_()
+            t.append(events_time(torch, stream, fn, 1))
+        return B * 1000.0 / float(np.mean(t))
+
+    forms = {
+        "batched_bf16x3_graph": None,
+        "batched_fp32_graph": form_rate(lambda: air.air_solve_batch(plans32, Yd, lam, mu, no, ncg, Xd)),
+        "batched_fp32_persistent": form_rate(
+            lambda: air.air_solve_batch_persistent(plans32, Yd, lam, mu, no, ncg, Xd)),
+    }
+
     # ---- plain single-slice path: one air_solve per slice, per-slice latency ----
     lat = {800: [], 200: []}
     for i in range(min(B, 4)):
         w = ws[i]
         for _ in range(2):
             flush.zero_()
-            t = events_time(torch, stream, lambda: air.air_solve(plans[i], Yd[i], w.lam, w.mu, w.n_outer,
+            t = events_time(torch, stream, lambda: air.air_solve(plans32[i], Yd[i], w.lam, w.mu, w.n_outer,
                                                                   w.n_cg, Xd[i]), 1)
             lat[w.geom.n_views].append(t)
     plain_ms = [t for v in lat.values() for t in v]
 
     # ---- dominant kernel: the backprojector on a 512^2/800 slice ----
-    p800 = plans[0]
+    p800 = plans32[0]
     g8 = ws[0].geom
     zin = Yd[0]
     xout = torch.empty(g8.n ** 2, device=dev)
@@ -331,6 +373,19 @@ def main():
     air.air_project(p800, Xd[0], yout)
     t_fwd = events_time(torch, stream, lambda: air.air_project(p800, Xd[0], yout), 20)
     alg_bytes = 4 * (g8.n ** 2 + g8.n_views * g8.n_bins)       # read Z + write X (fwd: read X + write Y)
+    # single applications on the phantom and the measured sinogram, for the
+    # precision report (compared with the oracle in the CPU-baseline leg)
+    ell0 = inputs.random_phantom(g8, ws[0].seed, ws[0].n_ellipses, ws[0].n_disks)
+    Xph = torch.as_tensor(inputs.rasterize(g8, ell0).astype(np.float32).ravel(), device=dev)
+    A_g = torch.empty(g8.n_views * g8.n_bins, device=dev)
+    air.air_project(p800, Xph, A_g)
+    atc32 = torch.empty(g8.n ** 2, device=dev)
+    atc16 = torch.empty(g8.n ** 2, device=dev)
+    air.air_filtered_backproject(p800, Yd[0], atc32)
+    air.air_filtered_backproject(plans[0], Yd[0], atc16)
+    torch.cuda.synchronize()
+    gpu_out = {"A": A_g.cpu().numpy(), "ATC_fp32": atc32.cpu().numpy(), "ATC_bf16x3": atc16.cpu().numpy(),
+               **final_images}
     peaks = load_peaks()
     # issue-limited roofline of the backprojector: warp instructions per
     # launch from the committed ncu capture of the same kernel and input
@@ -346,14 +401,15 @@ def main():
     slices = B * args.steps * world
     value = slices / (total_ms / 1000.0)
     e2e_value = slices / (e2e_total / 1000.0)
+    forms["batched_bf16x3_graph"] = B * args.steps / (float(sum(ms)) / 1000.0)
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    cpu = None
+    cpu, prec = None, None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline()
+        cpu, prec = cpu_baseline(gpu_out)
     line = {
         "metric": METRIC,
         "value": value,
@@ -369,11 +425,12 @@ def main():
         "data": "synthetic",
         "config": {"workload": "air512: 512x512 0.8 mm, 738 bins, 800 and 200 views, 30x8 split-Bregman",
                    "slices_per_step": B, "views_mix": "half 800, half 200",
-                   "form": "air_solve_batch (persistent kernel, CUDA graph)",
+                   "form": "air_solve_batch: grouped per-phase launches in a CUDA graph, BF16X3 filter",
                    "l2": "flushed between timed steps (256 MB write); working set > L2",
                    "parallelism": f"slices sharded over {world} GPU(s), no collective"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps * 1,
+        "gpu_launches": args.steps * launches_per_step,
+        "forms_slices_per_s": forms,
         "clocks": clk,
         "plain_gpu": {"path": "air_solve, one slice at a time",
                       "slices_per_s": 1000.0 * len(plain_ms) / sum(plain_ms),
@@ -395,6 +452,7 @@ def main():
                      "peak_src": "152 SMs x 4 issue/clk x max SM clock",
                      "sm_mhz_under_load": sm_mhz},
         "cpu_baseline": cpu,
+        "precision_vs_fp64_oracle": prec,
     }
     print(json.dumps(line), flush=True)
     if dist:

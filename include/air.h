@@ -169,12 +169,23 @@ AIR_API air_status air_solve(const air_plan *plan, const float *Y, float lambda,
 AIR_API air_status air_solve_host(const air_plan *plan, const float *Y_host, float lambda, float mu,
                           int n_outer, int n_cg, float *X_host, air_stream stream);
 
-/* Many independent slices of uneven geometry in one persistent kernel
- * launch (replayed from a CUDA graph): every slice i is solved as by
- * air_solve(plans[i], Y[i], lambda[i], mu[i], n_outer[i], n_cg[i], X[i]).
- * plans must be distinct (each slice uses its plan's workspace).  Arrays of
- * length n are HOST arrays; Y[i], X[i] are device pointers. */
+/* Many independent slices of uneven geometry solved together: every slice i
+ * is solved as by air_solve(plans[i], Y[i], lambda[i], mu[i], n_outer[i],
+ * n_cg[i], X[i]).  The programs advance phase by phase, each phase one
+ * grouped launch over the tiles of all slices (FP32 and BF16X3 plans may be
+ * mixed); the launch sequence is captured into a CUDA graph once per batch
+ * composition and replayed by later calls with the same arguments.  plans
+ * must be distinct (each slice uses its plan's workspace).  Arrays of length
+ * n are HOST arrays; Y[i], X[i] are device pointers.  Returns after the
+ * batch has finished (synchronises `stream`). */
 AIR_API air_status air_solve_batch(int n, air_plan *const *plans, const float *const *Y,
+                           const float *lambda, const float *mu, const int *n_outer,
+                           const int *n_cg, float *const *X, air_stream stream);
+/* The same batch in ONE persistent cooperative kernel launch (captured in a
+ * CUDA graph) whose blocks run every phase of every slice, separated by a
+ * grid barrier with a bounded wait (AIR_ERR_TIMEOUT if it gives up).  FP32
+ * plans only.  Synchronises `stream`. */
+AIR_API air_status air_solve_batch_persistent(int n, air_plan *const *plans, const float *const *Y,
                            const float *lambda, const float *mu, const int *n_outer,
                            const int *n_cg, float *const *X, air_stream stream);
 

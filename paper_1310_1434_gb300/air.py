@@ -29,7 +29,7 @@ EXPORTS = ["air_last_error", "air_plan_create", "air_plan_destroy", "air_plan_by
            "air_project",
            "air_filter", "air_backproject", "air_filtered_backproject", "air_filtered_backproject_noalloc",
            "air_framelet", "air_shrink",
-           "air_solve", "air_solve_host", "air_solve_batch", "air_server_create", "air_server_submit",
+           "air_solve", "air_solve_host", "air_solve_batch", "air_solve_batch_persistent", "air_server_create", "air_server_submit",
            "air_server_poll", "air_server_wait", "air_server_times", "air_server_destroy"]
 
 
@@ -83,6 +83,7 @@ def load(build_if_missing: bool = False):
         "air_solve": (i32, [P, P, f32, f32, i32, i32, P, P, P]),
         "air_solve_host": (i32, [P, P, f32, f32, i32, i32, P, P]),
         "air_solve_batch": (i32, [i32, P, P, P, P, P, P, P, P]),
+        "air_solve_batch_persistent": (i32, [i32, P, P, P, P, P, P, P, P]),
         "air_server_create": (i32, [ctypes.c_size_t, i32, ctypes.POINTER(P)]),
         "air_server_submit": (i32, [P, g, P, f32, f32, i32, i32, ctypes.POINTER(u64)]),
         "air_server_poll": (i32, [P, u64, P]),
@@ -234,15 +235,23 @@ def air_solve_host(plan: Plan, Y_host, lam: float, mu: float, n_outer: int, n_cg
                                  _ptr(X_host), _stream(stream)), "air_solve_host")
 
 
-def air_solve_batch(plans, Ys, lams, mus, n_outers, n_cgs, Xs, stream=None):
+def _batch(fn, name, plans, Ys, lams, mus, n_outers, n_cgs, Xs, stream):
     n = len(plans)
     VP = ctypes.c_void_p * n
-    _check(load().air_solve_batch(
-        n, ctypes.cast(VP(*[p.handle for p in plans]), ctypes.c_void_p),
-        ctypes.cast(VP(*[_ptr(y) for y in Ys]), ctypes.c_void_p),
-        ctypes.cast((ctypes.c_float * n)(*lams), ctypes.c_void_p),
-        ctypes.cast((ctypes.c_float * n)(*mus), ctypes.c_void_p),
-        ctypes.cast((ctypes.c_int * n)(*n_outers), ctypes.c_void_p),
-        ctypes.cast((ctypes.c_int * n)(*n_cgs), ctypes.c_void_p),
-        ctypes.cast(VP(*[_ptr(x) for x in Xs]), ctypes.c_void_p),
-        _stream(stream)), "air_solve_batch")
+    _check(fn(n, ctypes.cast(VP(*[p.handle for p in plans]), ctypes.c_void_p),
+              ctypes.cast(VP(*[_ptr(y) for y in Ys]), ctypes.c_void_p),
+              ctypes.cast((ctypes.c_float * n)(*lams), ctypes.c_void_p),
+              ctypes.cast((ctypes.c_float * n)(*mus), ctypes.c_void_p),
+              ctypes.cast((ctypes.c_int * n)(*n_outers), ctypes.c_void_p),
+              ctypes.cast((ctypes.c_int * n)(*n_cgs), ctypes.c_void_p),
+              ctypes.cast(VP(*[_ptr(x) for x in Xs]), ctypes.c_void_p),
+              _stream(stream)), name)
+
+
+def air_solve_batch(plans, Ys, lams, mus, n_outers, n_cgs, Xs, stream=None):
+    _batch(load().air_solve_batch, "air_solve_batch", plans, Ys, lams, mus, n_outers, n_cgs, Xs, stream)
+
+
+def air_solve_batch_persistent(plans, Ys, lams, mus, n_outers, n_cgs, Xs, stream=None):
+    _batch(load().air_solve_batch_persistent, "air_solve_batch_persistent", plans, Ys, lams, mus, n_outers,
+           n_cgs, Xs, stream)

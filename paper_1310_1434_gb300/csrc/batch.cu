@@ -1,12 +1,23 @@
-// air_solve_batch: many slices of uneven geometry solved by one persistent
-// cooperative kernel (k_persistent) that runs every phase of every slice's
-// split-Bregman program, separated by a bounded grid barrier.  The launch is
-// captured once per batch composition into a CUDA graph and replayed.
+// Batched solves of many independent slices of uneven geometry.
+//
+// air_solve_batch: the split-Bregman programs of all slices advance phase by
+// phase; each phase is one grouped launch of that op's kernel over the tiles
+// of every slice (plus the tensor-core filter of each BF16X3 slice), and the
+// whole sequence is captured once per batch composition into a CUDA graph
+// that later calls replay.
+//
+// air_solve_batch_persistent: the same programs in ONE persistent
+// cooperative kernel (k_persistent) that runs every phase with a bounded grid
+// barrier in between, also captured in a graph.  It has one register and
+// shared-memory budget for every op, which costs occupancy on the projector
+// pair; it is kept for callers that want a single launch.
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <vector>
 
 #include "host_common.h"
+#include "ramp_tc.h"
 #include "tiles.cuh"
 
 using namespace air;
@@ -19,11 +30,11 @@ struct BatchGraph {
     cudaGraphExec_t exec = nullptr;
     char *dmem = nullptr;
     BatchCtl *ctl = nullptr;
-    int device = -1;
+    std::vector<const air_plan *> tc_plans;   // plans whose status is checked after a run
 };
 
 std::mutex g_batch_mu;
-BatchGraph g_batch;
+BatchGraph g_grouped, g_persistent;
 
 void release(BatchGraph &b) {
     if (b.exec) cudaGraphExecDestroy(b.exec);
@@ -33,18 +44,20 @@ void release(BatchGraph &b) {
     b.cap = cap;
 }
 
-}  // namespace
+struct Batch {
+    std::vector<SliceDesc> slices;
+    std::vector<std::vector<Phase>> progs;
+    size_t nphases = 0;
+    std::vector<uintptr_t> key;
+};
 
-extern "C" air_status air_solve_batch(int n, air_plan *const *plans, const float *const *Y,
-                                      const float *lambda, const float *mu, const int *n_outer,
-                                      const int *n_cg, float *const *X, air_stream stream) {
+air_status prepare(int n, air_plan *const *plans, const float *const *Y, const float *lambda, const float *mu,
+                   const int *n_outer, const int *n_cg, float *const *X, cudaStream_t st, bool allow_tc, Batch *B) {
     if (n < 1 || n > 4096) return fail(AIR_ERR_INVALID_ARG, "n must be in 1..4096");
     if (!plans || !Y || !lambda || !mu || !n_outer || !n_cg || !X)
         return fail(AIR_ERR_INVALID_ARG, "NULL array argument");
-    const cudaStream_t st = (cudaStream_t)stream;
-    std::vector<SliceDesc> slices(n);
-    std::vector<std::vector<Phase>> progs(n);
-    size_t nphases = 0, smem = 0;
+    B->slices.resize(n);
+    B->progs.resize(n);
     for (int i = 0; i < n; ++i) {
         air_status s = check_solve_args(plans[i], Y[i], lambda[i], mu[i], n_outer[i], n_cg[i], X[i]);
         if (s != AIR_OK) return s;
@@ -52,78 +65,185 @@ extern "C" air_status air_solve_batch(int n, air_plan *const *plans, const float
         if ((s = check_dev_ptr(X[i], "X[i]")) != AIR_OK) return s;
         for (int k = 0; k < i; ++k)
             if (plans[k] == plans[i]) return fail(AIR_ERR_INVALID_ARG, "plans of a batch must be distinct");
-        if (plans[i]->geom.precision != AIR_PREC_FP32 && plans[i]->geom.filter == AIR_FILTER_RAMLAK)
-            return fail(AIR_ERR_INVALID_ARG, "air_solve_batch runs the FP32 filter; use FP32 plans");
-        slices[i] = solve_desc(plans[i], Y[i], lambda[i], mu[i], X[i], nullptr);
-        progs[i] = solve_program(n_outer[i], n_cg[i], false);
-        nphases = std::max(nphases, progs[i].size());
-        for (int op : {OP_RAMP, OP_SHRINK, OP_TRANSPOSE, OP_BWD}) smem = std::max(smem, tile_smem(slices[i], op));
+        const bool tc = plans[i]->geom.precision == AIR_PREC_BF16X3 && plans[i]->geom.filter == AIR_FILTER_RAMLAK;
+        if (tc && !allow_tc)
+            return fail(AIR_ERR_INVALID_ARG, "the persistent batch runs the FP32 filter; use FP32 plans");
+        B->slices[i] = solve_desc(plans[i], Y[i], lambda[i], mu[i], X[i], nullptr);
+        B->progs[i] = solve_program(n_outer[i], n_cg[i], tc);
+        B->nphases = std::max(B->nphases, B->progs[i].size());
     }
-    std::vector<Phase> prog(n * nphases, Phase{OP_NOP, 0});
-    for (int i = 0; i < n; ++i) std::memcpy(&prog[i * nphases], progs[i].data(), progs[i].size() * sizeof(Phase));
-
-    std::vector<uintptr_t> key;
-    key.reserve(8 * n + 2);
     int dev = 0;
     cudaGetDevice(&dev);
-    key.push_back((uintptr_t)dev);
-    key.push_back((uintptr_t)st);
+    B->key.push_back((uintptr_t)dev);
+    B->key.push_back((uintptr_t)st);
     for (int i = 0; i < n; ++i) {
         uint32_t lb, mb;
         std::memcpy(&lb, &lambda[i], 4);
         std::memcpy(&mb, &mu[i], 4);
-        key.insert(key.end(), {(uintptr_t)plans[i], (uintptr_t)Y[i], (uintptr_t)X[i], (uintptr_t)lb,
-                               (uintptr_t)mb, (uintptr_t)n_outer[i], (uintptr_t)n_cg[i]});
+        B->key.insert(B->key.end(), {(uintptr_t)plans[i], (uintptr_t)Y[i], (uintptr_t)X[i], (uintptr_t)lb,
+                                     (uintptr_t)mb, (uintptr_t)n_outer[i], (uintptr_t)n_cg[i]});
     }
+    return AIR_OK;
+}
 
-    std::lock_guard<std::mutex> lock(g_batch_mu);
-    if (g_batch.key != key || !g_batch.exec) {
-        release(g_batch);
-        const size_t b_slices = align_up(n * sizeof(SliceDesc), 256);
-        const size_t b_prog = align_up(prog.size() * sizeof(Phase), 256);
-        char *dmem = nullptr;
-        if (cudaMalloc(&dmem, b_slices + b_prog + 256) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(AIR_ERR_OOM, "batch table allocation failed");
-        }
-        g_batch.dmem = dmem;
-        SliceDesc *d_slices = (SliceDesc *)dmem;
-        Phase *d_prog = (Phase *)(dmem + b_slices);
-        g_batch.ctl = (BatchCtl *)(dmem + b_slices + b_prog);
-        cudaError_t e = cudaMemcpy(d_slices, slices.data(), n * sizeof(SliceDesc), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(d_prog, prog.data(), prog.size() * sizeof(Phase), cudaMemcpyHostToDevice);
-        const int grid = persistent_grid(smem);
-        if (e == cudaSuccess && grid <= 0) e = cudaErrorInvalidConfiguration;
-        // captured on a private stream (the caller's may be the legacy default
-        // stream, which cannot be captured); launched on the caller's stream
-        if (e == cudaSuccess && !g_batch.cap) e = cudaStreamCreateWithFlags(&g_batch.cap, cudaStreamNonBlocking);
-        const cudaStream_t cs = g_batch.cap;
-        cudaGraph_t graph = nullptr;
-        if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            cudaError_t e1 = cudaMemsetAsync(g_batch.ctl, 0, sizeof(BatchCtl), cs);
-            cudaError_t e2 = e1 == cudaSuccess
-                                 ? launch_persistent(d_slices, n, d_prog, (int)nphases, g_batch.ctl, grid, smem, cs)
-                                 : e1;
-            e = cudaStreamEndCapture(cs, &graph);
-            if (e2 != cudaSuccess) e = e2;
-        }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&g_batch.exec, graph, 0);
-        if (graph) cudaGraphDestroy(graph);
-        if (e != cudaSuccess) {
-            release(g_batch);
-            cudaGetLastError();
-            return fail(AIR_ERR_CUDA, std::string("batch graph build: ") + cudaGetErrorString(e));
-        }
-        g_batch.key = key;
-        g_batch.device = dev;
-    }
-    cudaError_t e = cudaGraphLaunch(g_batch.exec, st);
+air_status run_cached(BatchGraph &G, cudaStream_t st) {
+    cudaError_t e = cudaGraphLaunch(G.exec, st);
     if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("batch graph launch: ") + cudaGetErrorString(e));
     BatchCtl ctl{};
-    e = cudaMemcpyAsync(&ctl, g_batch.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st);
+    if (G.ctl) e = cudaMemcpyAsync(&ctl, G.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("batch solve: ") + cudaGetErrorString(e));
     if (ctl.error != 0) return fail(AIR_ERR_TIMEOUT, "a grid barrier of the batch kernel timed out");
+    for (const air_plan *p : G.tc_plans) {
+        air_status s = air_plan_status(p);
+        if (s != AIR_OK) return s;
+    }
     return AIR_OK;
+}
+
+air_status end_capture(BatchGraph &G, cudaStream_t cs, cudaError_t launch_err) {
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (launch_err != cudaSuccess) e = launch_err;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        release(G);
+        cudaGetLastError();
+        return fail(AIR_ERR_CUDA, std::string("batch graph build: ") + cudaGetErrorString(e));
+    }
+    return AIR_OK;
+}
+
+}  // namespace
+
+extern "C" air_status air_solve_batch(int n, air_plan *const *plans, const float *const *Y, const float *lambda,
+                                      const float *mu, const int *n_outer, const int *n_cg, float *const *X,
+                                      air_stream stream) {
+    const cudaStream_t st = (cudaStream_t)stream;
+    Batch B;
+    air_status s = prepare(n, plans, Y, lambda, mu, n_outer, n_cg, X, st, true, &B);
+    if (s != AIR_OK) return s;
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    BatchGraph &G = g_grouped;
+    if (G.key != B.key || !G.exec) {
+        release(G);
+        // phase by phase: one task list per op present in the phase
+        struct Launch { int op, off, ntasks, tiles; size_t smem; int slice, arg; };
+        std::vector<Task> tasks;
+        std::vector<Launch> launches;
+        for (size_t ph = 0; ph < B.nphases; ++ph) {
+            std::map<int, std::vector<int>> by_op;   // op -> slices
+            for (int i = 0; i < n; ++i)
+                if (ph < B.progs[i].size()) by_op[B.progs[i][ph].op].push_back(i);
+            for (auto &kv : by_op) {
+                const int op = kv.first;
+                if (op == OP_NOP) continue;
+                if (op == OP_RAMP_TC) {   // the tensor-core filter, slice by slice
+                    for (int i : kv.second) launches.push_back({op, 0, 0, 0, 0, i, B.progs[i][ph].arg});
+                    continue;
+                }
+                Launch L{op, (int)tasks.size(), 0, 0, 0, -1, 0};
+                for (int i : kv.second) {
+                    const int t = tiles_of(B.slices[i], op);
+                    if (t <= 0) continue;
+                    tasks.push_back({i, op, B.progs[i][ph].arg, L.tiles});
+                    L.tiles += t;
+                    L.smem = std::max(L.smem, tile_smem(B.slices[i], op));
+                }
+                L.ntasks = (int)tasks.size() - L.off;
+                if (L.ntasks > 0) launches.push_back(L);
+            }
+        }
+        const size_t b_slices = align_up(n * sizeof(SliceDesc), 256);
+        const size_t b_tasks = align_up(std::max<size_t>(tasks.size(), 1) * sizeof(Task), 256);
+        if (cudaMalloc(&G.dmem, b_slices + b_tasks) != cudaSuccess) {
+            cudaGetLastError();
+            G.dmem = nullptr;
+            return fail(AIR_ERR_OOM, "batch table allocation failed");
+        }
+        SliceDesc *d_slices = (SliceDesc *)G.dmem;
+        Task *d_tasks = (Task *)(G.dmem + b_slices);
+        cudaError_t e = cudaMemcpy(d_slices, B.slices.data(), n * sizeof(SliceDesc), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !tasks.empty())
+            e = cudaMemcpy(d_tasks, tasks.data(), tasks.size() * sizeof(Task), cudaMemcpyHostToDevice);
+        // captured on a private stream (the caller's may be the legacy default
+        // stream, which cannot be captured); launched on the caller's stream
+        if (e == cudaSuccess && !G.cap) e = cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            release(G);
+            return fail(AIR_ERR_CUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
+        }
+        const cudaStream_t cs = G.cap;
+        cudaError_t le = cudaSuccess;
+        for (const Launch &L : launches) {
+            if (L.op == OP_RAMP_TC) {
+                const SliceDesc &sd = B.slices[L.slice];
+                const float *src = L.arg == RSRC_Y ? sd.y : sd.z;
+                if (ramp_tc_apply(plans[L.slice], src, sd.zc, sd.cg, L.arg == RSRC_Z, cs) != AIR_OK) {
+                    const std::string msg = air_last_error();
+                    cudaGraph_t g = nullptr;
+                    cudaStreamEndCapture(cs, &g);
+                    if (g) cudaGraphDestroy(g);
+                    release(G);
+                    cudaGetLastError();
+                    return fail(AIR_ERR_CUDA, "batch graph build: " + msg);
+                }
+            } else {
+                le = launch_group(L.op, d_slices, d_tasks + L.off, L.ntasks, L.tiles, L.smem, cs);
+                if (le != cudaSuccess) break;
+            }
+        }
+        if ((s = end_capture(G, cs, le)) != AIR_OK) return s;
+        G.key = B.key;
+        for (int i = 0; i < n; ++i)
+            if (plans[i]->tc) G.tc_plans.push_back(plans[i]);
+    }
+    return run_cached(G, st);
+}
+
+extern "C" air_status air_solve_batch_persistent(int n, air_plan *const *plans, const float *const *Y,
+                                                 const float *lambda, const float *mu, const int *n_outer,
+                                                 const int *n_cg, float *const *X, air_stream stream) {
+    const cudaStream_t st = (cudaStream_t)stream;
+    Batch B;
+    air_status s = prepare(n, plans, Y, lambda, mu, n_outer, n_cg, X, st, false, &B);
+    if (s != AIR_OK) return s;
+    size_t smem = 0;
+    for (int i = 0; i < n; ++i)
+        for (int op : {OP_RAMP, OP_SHRINK, OP_TRANSPOSE, OP_BWD}) smem = std::max(smem, tile_smem(B.slices[i], op));
+    std::vector<Phase> prog(n * B.nphases, Phase{OP_NOP, 0});
+    for (int i = 0; i < n; ++i)
+        std::memcpy(&prog[i * B.nphases], B.progs[i].data(), B.progs[i].size() * sizeof(Phase));
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    BatchGraph &G = g_persistent;
+    if (G.key != B.key || !G.exec) {
+        release(G);
+        const size_t b_slices = align_up(n * sizeof(SliceDesc), 256);
+        const size_t b_prog = align_up(prog.size() * sizeof(Phase), 256);
+        if (cudaMalloc(&G.dmem, b_slices + b_prog + 256) != cudaSuccess) {
+            cudaGetLastError();
+            G.dmem = nullptr;
+            return fail(AIR_ERR_OOM, "batch table allocation failed");
+        }
+        SliceDesc *d_slices = (SliceDesc *)G.dmem;
+        Phase *d_prog = (Phase *)(G.dmem + b_slices);
+        G.ctl = (BatchCtl *)(G.dmem + b_slices + b_prog);
+        cudaError_t e = cudaMemcpy(d_slices, B.slices.data(), n * sizeof(SliceDesc), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d_prog, prog.data(), prog.size() * sizeof(Phase), cudaMemcpyHostToDevice);
+        const int grid = persistent_grid(smem);
+        if (e == cudaSuccess && grid <= 0) e = cudaErrorInvalidConfiguration;
+        if (e == cudaSuccess && !G.cap) e = cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            release(G);
+            return fail(AIR_ERR_CUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
+        }
+        cudaError_t le = cudaMemsetAsync(G.ctl, 0, sizeof(BatchCtl), G.cap);
+        if (le == cudaSuccess) le = launch_persistent(d_slices, n, d_prog, (int)B.nphases, G.ctl, grid, smem, G.cap);
+        if ((s = end_capture(G, G.cap, le)) != AIR_OK) return s;
+        G.key = B.key;
+    }
+    return run_cached(G, st);
 }

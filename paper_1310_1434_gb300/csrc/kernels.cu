@@ -110,6 +110,68 @@ k_tasks(const SliceDesc *__restrict__ slices, const Task *__restrict__ tasks, in
     run_tile(stage_desc(slices, t.slice, &sd, &staged), t.op, t.arg, b - t.tile0, sm);
 }
 
+// Grouped form of one op: the tiles of many slices in one launch, the
+// kernel specialised for the op (its own register budget).
+template <int OP>
+__global__ void __launch_bounds__(AIR_THREADS)
+k_group(const SliceDesc *__restrict__ slices, const Task *__restrict__ tasks, int ntasks) {
+    extern __shared__ __align__(16) float sm[];
+    __shared__ __align__(16) SliceDesc sd;
+    const int b = blockIdx.x;
+    int lo = 0, hi = ntasks - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tasks[mid].tile0 <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const Task t = tasks[lo];
+    int staged = -1;
+    const SliceDesc &s = stage_desc(slices, t.slice, &sd, &staged);
+    const int tile = b - t.tile0;
+    if constexpr (OP == OP_FWD) tile_fwd(s, t.arg, tile);
+    else if constexpr (OP == OP_RAMP) tile_ramp(s, t.arg, tile, sm);
+    else if constexpr (OP == OP_BWD) tile_bwd(s, t.arg, tile, sm);
+    else if constexpr (OP == OP_BWD_FIN) tile_bwd_fin(s, t.arg, tile);
+    else if constexpr (OP == OP_CG_A) tile_cg_a(s, tile);
+    else if constexpr (OP == OP_CG_B) tile_cg_b(s, tile);
+    else if constexpr (OP == OP_ZERO) tile_zero(s, tile);
+    else if constexpr (OP == OP_TRANSPOSE) tile_transpose(s, t.arg, tile, sm);
+    else if constexpr (OP == OP_SHRINK) {
+        ShrinkArgs a{s.x, t.arg ? s.b2 : s.b, t.arg ? s.b : s.b2, s.g, s.tau};
+        tile_shrink(s, a, tile, true, nullptr, sm);
+    }
+}
+
+template <int OP>
+static cudaError_t launch_group_op(const SliceDesc *d_slices, const Task *d_tasks, int ntasks, int total_tiles,
+                                   size_t smem, cudaStream_t st) {
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(k_group<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    k_group<OP><<<total_tiles, AIR_THREADS, smem, st>>>(d_slices, d_tasks, ntasks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group(int op, const SliceDesc *d_slices, const Task *d_tasks, int ntasks, int total_tiles,
+                         size_t smem, cudaStream_t st) {
+    if (ntasks <= 0 || total_tiles <= 0) return cudaSuccess;
+    switch (op) {
+    case OP_FWD: return launch_group_op<OP_FWD>(d_slices, d_tasks, ntasks, total_tiles, smem, st);
+    case OP_RAMP: return launch_group_op<OP_RAMP>(d_slices, d_tasks, ntasks, total_tiles, smem, st);
+    case OP_BWD: return launch_group_op<OP_BWD>(d_slices, d_tasks, ntasks, total_tiles, smem, st);
+    case OP_BWD_FIN: return launch_group_op<OP_BWD_FIN>(d_slices, d_tasks, ntasks, total_tiles, smem, st);
+    case OP_CG_A: return launch_group_op<OP_CG_A>(d_slices, d_tasks, ntasks, total_tiles, smem, st);
+    case OP_CG_B: return launch_group_op<OP_CG_B>(d_slices, d_tasks, ntasks, total_tiles, smem, st);
+    case OP_ZERO: return launch_group_op<OP_ZERO>(d_slices, d_tasks, ntasks, total_tiles, smem, st);
+    case OP_TRANSPOSE: return launch_group_op<OP_TRANSPOSE>(d_slices, d_tasks, ntasks, total_tiles, smem, st);
+    case OP_SHRINK: return launch_group_op<OP_SHRINK>(d_slices, d_tasks, ntasks, total_tiles, smem, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_tasks(const SliceDesc *d_slices, const Task *d_tasks, int ntasks,
                          int total_tiles, size_t smem, cudaStream_t st) {
     if (ntasks <= 0 || total_tiles <= 0) return cudaSuccess;

@@ -16,6 +16,10 @@ cudaError_t launch_op(int op, const SliceDesc &s, int arg, cudaStream_t st);
 cudaError_t launch_tasks(const SliceDesc *d_slices, const Task *d_tasks, int ntasks,
                          int total_tiles, size_t smem, cudaStream_t st);
 
+// One op over the tiles of many slices in one launch (tasks all of that op).
+cudaError_t launch_group(int op, const SliceDesc *d_slices, const Task *d_tasks, int ntasks, int total_tiles,
+                         size_t smem, cudaStream_t st);
+
 // Persistent batch solve: one cooperative launch runs every phase of every
 // slice's program, with a bounded grid barrier between phases.
 struct Phase {

@@ -400,9 +400,9 @@ air_status ramp_tc_create(air_plan *P) {
                       make_map(&R->map_b, R->b, R->kp, 3 * (uint64_t)R->np, TK, TN);
     if (e == cudaSuccess) {
         e = cudaFuncSetAttribute(k_ramp_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
-        if (e == cudaSuccess)
+        if (e == cudaSuccess)   // the largest any plan needs: the limit is per kernel, not per plan
             e = cudaFuncSetAttribute(k_split_near, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)((nb + 2 * NEAR) * sizeof(float)));
+                                     (int)((RAMP_MAX_BINS + 2 * NEAR) * sizeof(float)));
     }
     if (e != cudaSuccess || !maps) {
         cudaFree(R->mem);

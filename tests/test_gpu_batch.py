@@ -25,16 +25,18 @@ def cases():
             inputs._wl("b3", 80, 1.0, 64, 120, 6, 6, 3, 1e5, n_outer=3, n_cg=3, filter=0)]
 
 
-def test_batch_matches_single_slices():
+@pytest.mark.parametrize("form", ["grouped", "persistent"])
+def test_batch_matches_single_slices(form):
     ws = cases()
+    solve = air.air_solve_batch if form == "grouped" else air.air_solve_batch_persistent
     Ys = [torch.as_tensor(f32(inputs.make_case(w)[2]).ravel(), device=DEV) for w in ws]
     plans = [air.Plan(w.geom) for w in ws]
     Xb = [torch.empty(w.geom.n ** 2, device=DEV) for w in ws]
     for _ in range(2):   # the second call replays the cached graph
         for x in Xb:
             x.fill_(float("nan"))
-        air.air_solve_batch(plans, Ys, [w.lam for w in ws], [w.mu for w in ws], [w.n_outer for w in ws],
-                            [w.n_cg for w in ws], Xb)
+        solve(plans, Ys, [w.lam for w in ws], [w.mu for w in ws], [w.n_outer for w in ws],
+              [w.n_cg for w in ws], Xb)
         for w, p, Y, xb in zip(ws, plans, Ys, Xb):
             xs = torch.empty_like(xb)
             air.air_solve(p, Y, w.lam, w.mu, w.n_outer, w.n_cg, xs)
@@ -51,3 +53,20 @@ def test_batch_rejects_shared_plans():
     X1, X2 = torch.empty(w.geom.n ** 2, device=DEV), torch.empty(w.geom.n ** 2, device=DEV)
     with pytest.raises(air.AirError):
         air.air_solve_batch([p, p], [Y, Y], [1e-3, 1e-3], [1.0, 1.0], [1, 1], [1, 1], [X1, X2])
+
+
+def test_grouped_batch_mixes_precisions():
+    import dataclasses
+    ws = cases()[:3]
+    geoms = [dataclasses.replace(w.geom, precision=1) if i % 2 == 0 else w.geom for i, w in enumerate(ws)]
+    Ys = [torch.as_tensor(f32(inputs.make_case(w)[2]).ravel(), device=DEV) for w in ws]
+    plans = [air.Plan(g) for g in geoms]
+    Xb = [torch.empty(w.geom.n ** 2, device=DEV) for w in ws]
+    air.air_solve_batch(plans, Ys, [w.lam for w in ws], [w.mu for w in ws], [w.n_outer for w in ws],
+                        [w.n_cg for w in ws], Xb)
+    for w, p, Y, xb in zip(ws, plans, Ys, Xb):
+        xs = torch.empty_like(xb)
+        air.air_solve(p, Y, w.lam, w.mu, w.n_outer, w.n_cg, xs)
+        torch.cuda.synchronize()
+        a, b = xb.cpu().numpy().astype(np.float64), xs.cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b), w.name
