@@ -51,7 +51,51 @@ def parse():
     ap.add_argument("--kernel", default=None, choices=["fwd", "bwd", "ramp", "shrink", "solve", "plain"],
                     help="profiling mode: run one operator on the 512^2/800-view slice --reps times")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests in each bounded serving trace (0 skips the serving measurement)")
     return ap.parse_args()
+
+
+def serve_trace(air, n_req: int, rate_hz: float, cache: dict, seed: int = 7):
+    """Replays a bounded prefix of the serving trace (Poisson arrivals, sizes
+    256/512/1024 x 200/400/800 views, 30x8 each, 120 GB budget) and returns
+    latency percentiles and throughput.  Sinograms are generated before the
+    clock starts, one per distinct geometry."""
+    trace = inputs.serving_trace(count=n_req, rate_hz=rate_hz, seed=seed)
+    data = []
+    for t_arr, w in trace:
+        key = (w.geom.n, w.geom.n_views)
+        if key not in cache:
+            cache[key] = inputs.make_case(w)[2].astype(np.float32).ravel()
+        data.append((t_arr, w, cache[key]))
+    srv = cache.setdefault("server", air.Server(120 * (1 << 30), max_slots=64))
+    t0 = time.perf_counter()
+    ids = []
+    for t_arr, w, Y in data:
+        dt = t0 + t_arr - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        ids.append((srv.submit(w.geom, Y, w.lam, w.mu, w.n_outer, w.n_cg), w))
+    lat, lat512, ends, starts = [], [], [], []
+    for rid, w in ids:
+        while True:
+            try:
+                tm = srv.times(rid)
+                break
+            except air.AirError:
+                time.sleep(0.0005)
+        srv.poll(rid, w.geom.n)
+        lat.append(tm[2] - tm[0])
+        if w.geom.n == 512:
+            lat512.append(tm[2] - tm[0])
+        starts.append(tm[0])
+        ends.append(tm[2])
+    makespan = max(ends) - min(starts)
+    return {"requests": n_req, "arrival_rate_hz": rate_hz,
+            "requests_per_s": n_req / makespan, "makespan_s": makespan,
+            "p50_ms": 1000 * float(np.percentile(lat, 50)), "p99_ms": 1000 * float(np.percentile(lat, 99)),
+            "p50_ms_512": 1000 * float(np.percentile(lat512, 50)) if lat512 else None,
+            "p99_ms_512": 1000 * float(np.percentile(lat512, 99)) if lat512 else None}
 
 
 def run_kernel(args):
@@ -351,6 +395,18 @@ def main():
             lambda: air.air_solve_batch_persistent(plans32, Yd, lam, mu, no, ncg, Xd)),
     }
 
+    # ---- serving: continuous batching of a bounded Poisson trace ----
+    serving = None
+    if args.serve_requests > 0:
+        cache = {}
+        serve_trace(air, 9, 1000.0, cache, seed=11)              # warm-up: fills the plan pool
+        stated = serve_trace(air, args.serve_requests, 200.0, cache)
+        sustain = serve_trace(air, args.serve_requests, 0.7 * stated["requests_per_s"], cache, seed=8)
+        cache["server"].close()
+        serving = {"stated_rate_200_per_s": stated, "sustainable_rate": sustain,
+                   "note": "bounded prefix of the 2000-request trace; 200/s exceeds capacity, so "
+                           "latency there includes queueing"}
+
     # ---- plain single-slice path: one air_solve per slice, per-slice latency ----
     lat = {800: [], 200: []}
     for i in range(min(B, 4)):
@@ -437,6 +493,7 @@ def main():
                       "p50_ms": float(np.percentile(plain_ms, 50)), "p99_ms": float(np.percentile(plain_ms, 99)),
                       "ms_800_views": float(np.mean(lat[800])) if lat[800] else None,
                       "ms_200_views": float(np.mean(lat[200])) if lat[200] else None},
+        "serving": serving,
         "latency_batch": {"p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
                           "note": "every slice of a batch completes with the batch"},
         "projector": {"fwd_ms": t_fwd, "bwd_ms": t_bwd, "alg_bytes": alg_bytes,

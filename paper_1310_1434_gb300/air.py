@@ -255,3 +255,54 @@ def air_solve_batch(plans, Ys, lams, mus, n_outers, n_cgs, Xs, stream=None):
 def air_solve_batch_persistent(plans, Ys, lams, mus, n_outers, n_cgs, Xs, stream=None):
     _batch(load().air_solve_batch_persistent, "air_solve_batch_persistent", plans, Ys, lams, mus, n_outers,
            n_cgs, Xs, stream)
+
+
+class Server:
+    """Continuous-batching reconstruction server (air_server_*)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 64):
+        h = ctypes.c_void_p()
+        _check(load().air_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h)),
+               "air_server_create")
+        self.handle = h.value
+
+    def submit(self, geom, Y_host, lam: float, mu: float, n_outer: int, n_cg: int) -> int:
+        import numpy as np
+        g = Geometry.of(geom).c()
+        Y = np.ascontiguousarray(Y_host, dtype=np.float32)
+        rid = ctypes.c_uint64()
+        _check(load().air_server_submit(self.handle, ctypes.byref(g), Y.ctypes.data, float(lam), float(mu),
+                                        int(n_outer), int(n_cg), ctypes.byref(rid)), "air_server_submit")
+        return rid.value
+
+    def poll(self, rid: int, n: int):
+        """The image (n*n float32) once finished, else None."""
+        import numpy as np
+        X = np.empty(n * n, np.float32)
+        st = load().air_server_poll(self.handle, rid, X.ctypes.data)
+        if st == AIR_ERR_NOT_READY:
+            return None
+        _check(st, "air_server_poll")
+        return X
+
+    def wait(self, rid: int, n: int):
+        import numpy as np
+        X = np.empty(n * n, np.float32)
+        _check(load().air_server_wait(self.handle, rid, X.ctypes.data), "air_server_wait")
+        return X
+
+    def times(self, rid: int):
+        t = (ctypes.c_double * 3)()
+        _check(load().air_server_times(self.handle, rid, t), "air_server_times")
+        return tuple(t)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().air_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -76,6 +76,39 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 }  // namespace air
 
 // -------------------------------------------------------------------- plan
+namespace air {
+// Backprojector view parts of a slice: enough (pixel tile, part) blocks for
+// ~4 waves of 6 resident blocks per SM, at most one part per view.
+int choose_bwd_parts(const SliceDesc &s) {
+    int sms = 148, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaGetLastError();
+    const int txy = tiles_bwd_xy(s), target = 4 * 6 * sms;
+    const int S = (target + txy - 1) / txy;
+    return S < 1 ? 1 : (S > s.V ? s.V : S);
+}
+
+// Device bytes a plan of this geometry will hold (the pieces of plan_build
+// and, for BF16X3, the tensor-core filter buffers), to within alignment.
+size_t plan_bytes_estimate(const air_geometry &g) {
+    SliceDesc s{};
+    s.n = g.n;
+    s.V = g.n_views;
+    s.nb = g.n_bins;
+    const size_t nn = (size_t)g.n * g.n, rays = (size_t)g.n_views * g.n_bins;
+    const size_t parts = (size_t)choose_bwd_parts(s);
+    size_t b = rays * sizeof(RayFx) + (size_t)g.n_views * 16 + (size_t)g.n_bins * 4;
+    b += nn * 4 * (7 + parts + 18 + 1);          // x r p q rhs0 g xt, parts, b b2, xbuf
+    b += rays * 4 * 3;                           // z zc ybuf
+    b += sizeof(CgState) + ((size_t)max_reduce_tiles(s) + 64) * 8 + 24 * 256;
+    if (g.precision == AIR_PREC_BF16X3) {
+        const size_t kp = ((size_t)g.n_bins + 63) / 64 * 64;
+        b += (size_t)g.n_views * 3 * kp * 2 + 3 * kp * kp * 2 + 1024;
+    }
+    return b;
+}
+}  // namespace air
+
 namespace {
 long long floor_div(long long a, long long b) {   // b > 0
     long long q = a / b;
@@ -146,21 +179,7 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     s.jmid = 0.5f * (nb - 1);
     s.filter = g.filter;
 
-    // backprojector view parts: enough (pixel tile, part) blocks for ~4
-    // waves of 6 resident blocks per SM, at most one part per view
-    int sms = 148;
-    {
-        int dev = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess)
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaGetLastError();
-    }
-    s.bwd_parts = 1;
-    {
-        const int txy = tiles_bwd_xy(s), target = 4 * 6 * sms;
-        int S = (target + txy - 1) / txy;
-        s.bwd_parts = S < 1 ? 1 : (S > V ? V : S);
-    }
+    s.bwd_parts = choose_bwd_parts(s);
     // carve one allocation
     struct Piece { void **dst; size_t bytes; };
     float *x, *r, *p, *q, *rhs0, *gg, *b, *b2, *z, *zc, *ybuf, *xbuf, *xt, *bpart;

@@ -34,6 +34,8 @@ SliceDesc solve_desc(const air_plan *P, const float *Y, float lambda, float mu, 
 air_status run_program_single(const air_plan *P, const SliceDesc &s, const std::vector<Phase> &prog,
                               cudaStream_t st);
 RayFx make_ray_fx(double px, double py, double ux, double uy, int n);
+int choose_bwd_parts(const SliceDesc &s);
+size_t plan_bytes_estimate(const air_geometry &g);
 air_status apply_filter(const air_plan *P, const SliceDesc &base, const float *src, float *dst,
                         cudaStream_t st);
 }  // namespace air

@@ -52,3 +52,12 @@ def test_null_arguments_rejected_on_host(lib):
     assert lib.air_solve(None, None, 0.0, 1.0, 1, 1, None, None, None) == air.AIR_ERR_INVALID_ARG
     assert lib.air_solve_batch(0, None, None, None, None, None, None, None, None) == air.AIR_ERR_INVALID_ARG
     assert lib.air_plan_destroy(None) == air.AIR_OK
+
+
+def test_server_arguments_rejected_on_host(lib):
+    h = ctypes.c_void_p()
+    assert lib.air_server_create(0, 4, ctypes.byref(h)) == air.AIR_ERR_INVALID_ARG
+    assert lib.air_server_create(1 << 30, 0, ctypes.byref(h)) == air.AIR_ERR_INVALID_ARG
+    assert lib.air_server_create(1 << 30, 4, None) == air.AIR_ERR_INVALID_ARG
+    assert lib.air_server_poll(None, 1, None) == air.AIR_ERR_INVALID_ARG
+    assert lib.air_server_destroy(None) == air.AIR_OK
