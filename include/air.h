@@ -89,6 +89,18 @@ AIR_API const char *air_last_error(void);
  * owns all of it; free with air_plan_destroy.  Synchronous. */
 AIR_API air_status air_plan_create(const air_geometry *geom, air_plan **out);
 AIR_API air_status air_plan_destroy(air_plan *plan);
+/* Kernel configuration of a plan.  air_plan_create times the projector's
+ * tile shape (views per block: 1, 2, 4 or 8, with 256/that bins) and the
+ * backprojector's split of the views over blocks on the plan's geometry and
+ * keeps the fastest (cached per geometry for the life of the process).
+ * air_plan_tune overrides the choice (AIR_ERR_INVALID_ARG outside the
+ * allowed values: bwd_view_parts in 1..*bwd_view_parts_max); results agree
+ * to rounding whatever the configuration (the summation order over views
+ * depends on the split).  Either pointer of air_plan_config may be NULL. */
+AIR_API air_status air_plan_tune(air_plan *plan, int fwd_views_per_block, int bwd_view_parts);
+AIR_API air_status air_plan_config(const air_plan *plan, int *fwd_views_per_block, int *bwd_view_parts,
+                                   int *bwd_view_parts_max);
+
 /* Status recorded on the device by the plan's kernels: AIR_OK, or
  * AIR_ERR_TIMEOUT if a bounded wait inside a kernel gave up (the kernel then
  * returned without its result).  Synchronises the device.  The status word is

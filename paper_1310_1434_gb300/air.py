@@ -26,6 +26,7 @@ PREC_FP32, PREC_BF16X3 = 0, 1
 
 # every symbol include/air.h declares
 EXPORTS = ["air_last_error", "air_plan_create", "air_plan_destroy", "air_plan_bytes", "air_plan_status",
+           "air_plan_tune", "air_plan_config",
            "air_project",
            "air_filter", "air_backproject", "air_filtered_backproject", "air_filtered_backproject_noalloc",
            "air_framelet", "air_shrink",
@@ -73,6 +74,8 @@ def load(build_if_missing: bool = False):
         "air_plan_destroy": (i32, [P]),
         "air_plan_bytes": (ctypes.c_size_t, [P]),
         "air_plan_status": (i32, [P]),
+        "air_plan_tune": (i32, [P, i32, i32]),
+        "air_plan_config": (i32, [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "air_project": (i32, [P, P, P, P]),
         "air_filter": (i32, [P, P, P, P]),
         "air_backproject": (i32, [P, P, P, P]),
@@ -191,6 +194,18 @@ def air_plan_destroy(plan: Plan):
 
 def air_plan_status(plan: Plan):
     _check(load().air_plan_status(plan.handle), "air_plan_status")
+
+
+def air_plan_tune(plan: Plan, fwd_views_per_block: int, bwd_view_parts: int):
+    _check(load().air_plan_tune(plan.handle, int(fwd_views_per_block), int(bwd_view_parts)), "air_plan_tune")
+
+
+def air_plan_config(plan: Plan):
+    """(views per projector block, backprojector view parts, largest allowed parts)."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().air_plan_config(plan.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "air_plan_config")
+    return a.value, b.value, c.value
 
 
 def air_project(plan: Plan, X, Y, stream=None):

@@ -18,8 +18,12 @@ LIB = os.path.join(OUT_DIR, "libair.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Host side: GCC 13's loop unswitching on switch statements (-O3) dropped
+# cases of the per-op switch in the batch builder's tile loop on aarch64,
+# so that every filter and backprojector launch went missing; host code is
+# not on the hot path, so that pass is off.
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-              "-I", INCLUDE] + ARCH
+              "-Xcompiler", "-fno-unswitch-loops", "-I", INCLUDE] + ARCH
 
 
 def _nvcc() -> str:

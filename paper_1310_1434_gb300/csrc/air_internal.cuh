@@ -12,7 +12,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/air.h"
+#include "air.h"   // from include/ (nvcc -I)
 
 #define AIR_THREADS 256
 
@@ -96,7 +96,8 @@ struct SliceDesc {
     float *x, *r, *p, *q, *rhs0, *g;   // n*n
     float *xt;                         // n*n: transposed copy of the projector's input
     float *bwd_part;                   // bwd_parts * n*n: the backprojector's per-view-part sums
-    int bwd_parts;                     // S: views split over S blocks per pixel tile
+    int bwd_parts;                     // S: views split over S blocks per pixel tile (tuned)
+    int fwd_vpb;                       // projector tile: views per block (1, 2, 4, 8; tuned)
     float *b, *b2;                     // 9*n*n each (Bregman variable, double-buffered)
     float *z, *zc;                     // V*nb
     const float *y;                    // V*nb measured sinogram
@@ -119,8 +120,10 @@ struct Task {
 };
 
 // ---------------------------------------------------- tile counts --------
+// projector tile: fwd_vpb views x (AIR_THREADS / fwd_vpb) bins, one ray per thread
 __host__ __device__ inline int tiles_fwd(const SliceDesc &s) {
-    return (s.V * s.nb + AIR_THREADS - 1) / AIR_THREADS;
+    const int bpb = AIR_THREADS / s.fwd_vpb;
+    return ((s.V + s.fwd_vpb - 1) / s.fwd_vpb) * ((s.nb + bpb - 1) / bpb);
 }
 __host__ __device__ inline int tiles_ramp(const SliceDesc &s) { return s.V; }
 // backprojector tile: 16 x 16 pixels x one of bwd_parts view parts; the

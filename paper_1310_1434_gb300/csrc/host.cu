@@ -1,7 +1,9 @@
 // Host side of the AIR library: plans (geometry tables + workspace), argument
 // checking, the stand-alone operator calls and the solver programs.
 #include <cmath>
+#include <algorithm>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -164,6 +166,112 @@ RayFx air::make_ray_fx(double px, double py, double ux, double uy, int n) {
     return r;
 }
 
+// ------------------------------------------------------------ autotuner
+// The projector's tile shape (views per block) and the backprojector's view
+// split are timed on the plan's own workspace (the kernels' work does not
+// depend on the data) and the fastest kept; results are cached per geometry
+// for the life of the process, so every plan of a geometry uses the same
+// configuration.
+namespace {
+struct TuneKey {
+    int n, V, nb;
+    double dx, dso, dg, beta0, arc;
+    bool operator<(const TuneKey &o) const {
+        return std::memcmp(this, &o, sizeof(TuneKey)) < 0;
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+}  // namespace
+
+namespace air {
+air_status autotune(air_plan *P) {
+    SliceDesc &s = P->desc;
+    TuneKey key;
+    std::memset(&key, 0, sizeof(key));
+    key.n = s.n;
+    key.V = s.V;
+    key.nb = s.nb;
+    key.dx = P->geom.pixel_mm;
+    key.dso = P->geom.dso_mm;
+    key.dg = fan_pitch(P->geom);
+    key.beta0 = P->geom.beta0;
+    key.arc = P->geom.arc;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            s.fwd_vpb = it->second.first;
+            s.bwd_parts = std::min(it->second.second, P->bwd_parts_max);
+            return AIR_OK;
+        }
+    }
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.x, 0, (size_t)s.n * s.n * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.z, 0, (size_t)s.V * s.nb * 4, st);
+    auto timed = [&](auto &&launch) -> float {
+        if (e != cudaSuccess) return 1e30f;
+        launch();                                   // warm-up
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r) launch();
+        cudaEventRecord(e1, st);
+        e = cudaEventSynchronize(e1);
+        float ms = 1e30f;
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    // projector: views per block
+    SliceDesc t = s;
+    t.ext_in = s.x;
+    t.ext_out = s.z;
+    int best_vpb = 1;
+    float best = 1e30f;
+    for (int vpb : {1, 2, 4, 8}) {
+        if (vpb > s.V) break;
+        t.fwd_vpb = vpb;
+        const float ms = timed([&] {
+            if (e == cudaSuccess) e = launch_op(OP_TRANSPOSE, t, SRC_EXT, st);
+            if (e == cudaSuccess) e = launch_op(OP_FWD, t, SRC_EXT, st);
+        });
+        if (ms < best * 0.98f) {
+            best = ms;
+            best_vpb = vpb;
+        }
+    }
+    // backprojector: view split around the heuristic's choice
+    t = s;
+    t.ext_in = s.z;
+    t.ext_out = s.r;
+    const int S0 = s.bwd_parts;
+    int best_S = S0;
+    best = 1e30f;
+    for (int S : {S0, std::max(1, S0 / 4), std::max(1, S0 / 2), std::min(P->bwd_parts_max, 2 * S0)}) {
+        t.bwd_parts = S;
+        const float ms = timed([&] {
+            if (e == cudaSuccess) e = launch_op(OP_BWD, t, BWD_PLAIN, st);
+            if (e == cudaSuccess && S > 1) e = launch_op(OP_BWD_FIN, t, BWD_PLAIN, st);
+        });
+        if (ms < best * 0.98f) {
+            best = ms;
+            best_S = S;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("autotuning: ") + cudaGetErrorString(e));
+    s.fwd_vpb = best_vpb;
+    s.bwd_parts = best_S;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = {best_vpb, best_S};
+    return AIR_OK;
+}
+}  // namespace air
+
 air_status plan_build(const air_geometry *geom, air_plan *P) {
     const air_geometry &g = *geom;
     const int n = g.n, V = g.n_views, nb = g.n_bins;
@@ -179,7 +287,10 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     s.jmid = 0.5f * (nb - 1);
     s.filter = g.filter;
 
+    s.fwd_vpb = 1;
     s.bwd_parts = choose_bwd_parts(s);
+    // the autotuner may pick up to twice the heuristic's view split
+    const int parts_max = std::min(V, 2 * s.bwd_parts);
     // carve one allocation
     struct Piece { void **dst; size_t bytes; };
     float *x, *r, *p, *q, *rhs0, *gg, *b, *b2, *z, *zc, *ybuf, *xbuf, *xt, *bpart;
@@ -191,7 +302,7 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     const size_t npart = (size_t)max_reduce_tiles(s) + 64;
     std::vector<Piece> pieces = {
         {(void **)&ray, rays * sizeof(RayFx)}, {(void **)&view, (size_t)V * sizeof(float4)},
-        {(void **)&xt, nn * 4}, {(void **)&bpart, (size_t)s.bwd_parts * nn * 4},
+        {(void **)&xt, nn * 4}, {(void **)&bpart, (size_t)parts_max * nn * 4},
         {(void **)&taps, (size_t)nb * sizeof(float)},
         {(void **)&x, nn * 4}, {(void **)&r, nn * 4}, {(void **)&p, nn * 4}, {(void **)&q, nn * 4},
         {(void **)&rhs0, nn * 4}, {(void **)&gg, nn * 4}, {(void **)&b, 9 * nn * 4}, {(void **)&b2, 9 * nn * 4},
@@ -266,6 +377,7 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     P->desc = s;
     P->mem = mem;
     P->bytes = total;
+    P->bwd_parts_max = parts_max;
     P->ybuf = ybuf;
     P->xbuf = xbuf;
     cudaGetDevice(&P->device);
@@ -275,6 +387,12 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
             cudaFree(mem);
             return st;
         }
+    }
+    air_status st = autotune(P);
+    if (st != AIR_OK) {
+        ramp_tc_destroy(P);
+        cudaFree(mem);
+        return st;
     }
     return AIR_OK;
 }
@@ -306,6 +424,26 @@ extern "C" air_status air_plan_destroy(air_plan *P) {
 }
 
 extern "C" size_t air_plan_bytes(const air_plan *P) { return P ? P->bytes + P->tc_bytes : 0; }
+
+extern "C" air_status air_plan_tune(air_plan *P, int fwd_views_per_block, int bwd_view_parts) {
+    if (!P) return fail(AIR_ERR_INVALID_ARG, "plan is NULL");
+    const int v = fwd_views_per_block;
+    if (v != 1 && v != 2 && v != 4 && v != 8) return fail(AIR_ERR_INVALID_ARG, "fwd_views_per_block must be 1, 2, 4 or 8");
+    if (bwd_view_parts < 1 || bwd_view_parts > P->bwd_parts_max)
+        return fail(AIR_ERR_INVALID_ARG, "bwd_view_parts must be in 1.." + std::to_string(P->bwd_parts_max));
+    P->desc.fwd_vpb = v;
+    P->desc.bwd_parts = bwd_view_parts;
+    return AIR_OK;
+}
+
+extern "C" air_status air_plan_config(const air_plan *P, int *fwd_views_per_block, int *bwd_view_parts,
+                                      int *bwd_view_parts_max) {
+    if (!P) return fail(AIR_ERR_INVALID_ARG, "plan is NULL");
+    if (fwd_views_per_block) *fwd_views_per_block = P->desc.fwd_vpb;
+    if (bwd_view_parts) *bwd_view_parts = P->desc.bwd_parts;
+    if (bwd_view_parts_max) *bwd_view_parts_max = P->bwd_parts_max;
+    return AIR_OK;
+}
 
 extern "C" air_status air_plan_status(const air_plan *P) {
     if (!P) return fail(AIR_ERR_INVALID_ARG, "plan is NULL");

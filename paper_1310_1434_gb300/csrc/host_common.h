@@ -18,6 +18,7 @@ struct air_plan {
     float *xbuf = nullptr;
     void *tc = nullptr;        // tensor-core filter resources (AIR_PREC_BF16X3)
     size_t tc_bytes = 0;
+    int bwd_parts_max = 1;     // view parts the backprojector's part buffer holds
 };
 
 namespace air {
@@ -35,6 +36,7 @@ air_status run_program_single(const air_plan *P, const SliceDesc &s, const std::
                               cudaStream_t st);
 RayFx make_ray_fx(double px, double py, double ux, double uy, int n);
 int choose_bwd_parts(const SliceDesc &s);
+air_status autotune(air_plan *P);
 size_t plan_bytes_estimate(const air_geometry &g);
 air_status apply_filter(const air_plan *P, const SliceDesc &base, const float *src, float *dst,
                         cudaStream_t st);

@@ -50,8 +50,15 @@ __device__ __forceinline__ void tile_fwd(const SliceDesc &s, int arg, int tile) 
     if (arg == SRC_P && s.cg->stop) return;
     const float *src = arg == SRC_X ? s.x : (arg == SRC_P ? s.p : s.ext_in);
     float *dst = arg == SRC_EXT ? s.ext_out : s.z;
-    const int idx = tile * AIR_THREADS + threadIdx.x;
-    if (idx >= s.V * s.nb) return;
+    // tile = (view group, bin range); a warp holds neighbouring bins of one
+    // view, and the warps of a block neighbouring views, whose rays walk
+    // neighbouring paths through the image
+    const int bpb = AIR_THREADS / s.fwd_vpb;
+    const int nbt = (s.nb + bpb - 1) / bpb;
+    const int v = (tile / nbt) * s.fwd_vpb + threadIdx.x / bpb;
+    const int j = (tile % nbt) * bpb + threadIdx.x % bpb;
+    if (v >= s.V || j >= s.nb) return;
+    const int idx = v * s.nb + j;
     const RayFx r = s.ray[idx];
     dst[idx] = s.dx * fx_ray(src, s.xt, s.n, r);
 }

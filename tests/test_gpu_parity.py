@@ -279,3 +279,35 @@ def test_full_size_solve_matches_stored_oracle(w):
     Xg, rg = run_solve(w.geom, Y, w.lam, w.mu, w.n_outer, w.n_cg)
     assert rel(Xg, ref["X"].astype(np.float64).ravel()) <= TOL_SOLVE
     assert np.max(np.abs(rg - ref["resid"]) / ref["resid"]) <= 1e-3
+
+
+def test_every_tuned_configuration_matches_oracle():
+    # the autotuner's choices change tile shapes and the view split, never the
+    # result beyond rounding; the projector's per-ray sums do not depend on
+    # the tile shape at all
+    g = inputs.Geometry(96, 1.2, 120, 150, beta0=0.3)
+    og = ogeom(g)
+    X = f32(phantom_image(g, 8))
+    Y = f32(inputs.noisy_sinogram(inputs.ellipse_line_integrals(g, inputs.random_phantom(g, 9, 6, 3)), 2e4, 9))
+    plan = air.Plan(g)
+    vpb0, S0, Smax = air.air_plan_config(plan)
+    assert vpb0 in (1, 2, 4, 8) and 1 <= S0 <= Smax
+    A_ref, ATC_ref = oracle.project(og, X).ravel(), oracle.filtered_backproject(og, Y).ravel()
+    Xd, Yd = dev(X), dev(Y)
+    first = None
+    for vpb in (1, 2, 4, 8):
+        for S in sorted({1, max(1, Smax // 2), Smax}):
+            air.air_plan_tune(plan, vpb, S)
+            Ad = torch.empty(g.n_views * g.n_bins, device=DEV)
+            air.air_project(plan, Xd, Ad)
+            Bd = torch.empty(g.n * g.n, device=DEV)
+            air.air_filtered_backproject(plan, Yd, Bd)
+            a, b = host(Ad), host(Bd)
+            assert rel(a, A_ref) <= TOL_OP and rel(b, ATC_ref) <= TOL_OP, (vpb, S)
+            if first is None:
+                first = a
+            assert np.array_equal(a, first)
+    with pytest.raises(air.AirError):
+        air.air_plan_tune(plan, 3, 1)
+    with pytest.raises(air.AirError):
+        air.air_plan_tune(plan, 1, Smax + 1)
