@@ -5,8 +5,8 @@ equiangular fan beam (source-isocentre 850 mm, source-detector 1450 mm),
 738 bins, 800 views (full) and 200 views (25 %), seeded ellipse + disk
 phantoms with Poisson noise at 2e4 photons/ray, lambda = 3e-4, mu = 1,
 30 split-Bregman x 8 CG iterations.  One step = one batch of B slices (half
-800-view, half 200-view) solved by the persistent batched kernel
-(air_solve_batch).  value = slices/s on the device with inputs resident;
+800-view, half 200-view) solved by air_solve_batch (grouped per-phase
+launches captured in a CUDA graph, split-BF16 tensor-core filter).  value = slices/s on the device with inputs resident;
 e2e = the same with pinned host buffers copied in and out inside the timed
 region.  The batch's working set (~60 MB per slice) exceeds L2 and L2 is
 also flushed between timed steps.
@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--impl", default="air", choices=["air", "reference"])
     ap.add_argument("--batch", type=int, default=8, help="slices per step (even: half 800, half 200 views)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", default=None, choices=["fwd", "bwd", "ramp", "shrink", "solve", "plain"],
+    ap.add_argument("--kernel", default=None, choices=["fwd", "bwd", "ramp", "shrink", "solve", "plain", "batch"],
                     help="profiling mode: run one operator on the 512^2/800-view slice --reps times")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--serve-requests", type=int, default=24,
@@ -98,6 +98,31 @@ def serve_trace(air, n_req: int, rate_hz: float, cache: dict, seed: int = 7):
             "p99_ms_512": 1000 * float(np.percentile(lat512, 99)) if lat512 else None}
 
 
+def segment_count(geom) -> int:
+    """nnz(A): ray-pixel intersections of every ray of the geometry.
+
+    A line crossing a grid visits one cell more than the grid lines it
+    crosses, so each ray clipped to the image square contributes
+    |ix_out - ix_in| + |iy_out - iy_in| + 1 pixels (exact for rays through
+    no grid vertex; a measure of the algorithmic work, not a step of A).
+    """
+    src, u = inputs.ray_lines(geom)
+    half = 0.5 * geom.n * geom.pixel_mm
+    sx, sy = np.broadcast_to(src[..., 0], u.shape[:2]), np.broadcast_to(src[..., 1], u.shape[:2])
+    ux, uy = u[..., 0], u[..., 1]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        tx0, tx1 = (-half - sx) / ux, (half - sx) / ux
+        ty0, ty1 = (-half - sy) / uy, (half - sy) / uy
+    t_in = np.maximum(np.minimum(tx0, tx1), np.minimum(ty0, ty1))
+    t_out = np.minimum(np.maximum(tx0, tx1), np.maximum(ty0, ty1))
+    hit = t_out > t_in
+    to_px = lambda c: np.clip(np.floor((c + half) / geom.pixel_mm), 0, geom.n - 1)
+    ix0, ix1 = to_px(sx + t_in * ux), to_px(sx + t_out * ux)
+    iy0, iy1 = to_px(sy + t_in * uy), to_px(sy + t_out * uy)
+    cells = np.abs(ix1 - ix0) + np.abs(iy1 - iy0) + 1
+    return int(np.sum(np.where(hit, cells, 0)))
+
+
 def run_kernel(args):
     """Runs one operator of the hot path --reps times (for ncu captures)."""
     import torch
@@ -120,6 +145,13 @@ def run_kernel(args):
            "shrink": lambda: air.air_shrink(plan, Xd, b, gg, w.lam / w.mu),
            "solve": lambda: air.air_solve(plan, Yd, w.lam, w.mu, w.n_outer, w.n_cg, X2),
            "plain": lambda: air.air_solve(plan, Yd, w.lam, w.mu, 1, 2, X2)}
+    if args.kernel == "batch":   # the timed step: one batch as bench times it
+        ws = workloads(max(2, args.batch), 0)
+        Ys = [torch.as_tensor(inputs.make_case(v)[2].astype(np.float32).ravel(), device="cuda") for v in ws]
+        Xs = [torch.empty(v.geom.n ** 2, device="cuda") for v in ws]
+        bplans = [air.Plan(dataclasses.replace(v.geom, precision=1)) for v in ws]
+        ops["batch"] = lambda: air.air_solve_batch(bplans, Ys, [v.lam for v in ws], [v.mu for v in ws],
+                                                   [v.n_outer for v in ws], [v.n_cg for v in ws], Xs)
     for _ in range(args.reps):
         ops[args.kernel]()
     torch.cuda.synchronize()
@@ -443,11 +475,12 @@ def main():
     gpu_out = {"A": A_g.cpu().numpy(), "ATC_fp32": atc32.cpu().numpy(), "ATC_bf16x3": atc16.cpu().numpy(),
                **final_images}
     peaks = load_peaks()
-    # issue-limited roofline of the backprojector: warp instructions per
-    # launch from the committed ncu capture of the same kernel and input
-    inst_per_launch = BWD_WARP_INST_512_V800
+    # issue-limited roofline of the backprojector: algorithmic work = nnz(A)
+    # segment evaluations per application; peak = SMs x 4 warp issues/clk x
+    # 32 lanes x max SM clock / SEG_INST thread-instructions per segment
+    nnz = segment_count(g8)
+    seg_peak = 152 * 4 * 32 * peaks["sm_max_mhz"] * 1e6 / SEG_INST / 1e9     # Gsegment/s
     sm_mhz = clk.get("sm_mhz") or peaks["sm_max_mhz"]
-    issue_peak = 152 * 4 * peaks["sm_max_mhz"] * 1e6 / 1e9     # G warp-instructions/s at max clock
 
     # ---- reduce over ranks (max time) ----
     t_rank = torch.tensor([total_ms, float(np.sum(e2e_ms))], dtype=torch.float64, device=dev)
@@ -500,13 +533,16 @@ def main():
                       "fwd_hbm_gbs": alg_bytes / (t_fwd * 1e-3) / 1e9,
                       "bwd_hbm_gbs": alg_bytes / (t_bwd * 1e-3) / 1e9,
                       "hbm_frac_of_measured": alg_bytes / (t_bwd * 1e-3) / 1e9 / peaks["hbm_gbs"]},
-        "roofline": {"kernel": "backprojector (k_op<OP_BWD>), 512^2 / 800 views",
+        "roofline": {"kernel": "backprojector (strip sweep, k_op<OP_BWD>), 512^2 / 800 views / 738 bins",
                      "bound": "alu",
-                     "achieved": inst_per_launch / (t_bwd * 1e-3) / 1e9 if inst_per_launch else None,
-                     "peak": issue_peak, "unit": "Gwarp-inst/s",
-                     "frac": (inst_per_launch / (t_bwd * 1e-3) / 1e9 / issue_peak) if inst_per_launch else None,
+                     "achieved": nnz / (t_bwd * 1e-3) / 1e9,
+                     "peak": seg_peak, "unit": "Gsegment/s",
+                     "frac": nnz / (t_bwd * 1e-3) / 1e9 / seg_peak,
                      "traffic": BWD_DRAM_BYTES_512_V800,
-                     "peak_src": "152 SMs x 4 issue/clk x max SM clock",
+                     "segments_per_launch": nnz,
+                     "peak_src": f"152 SMs x 4 issue/clk x 32 lanes x {peaks['sm_max_mhz']:.0f} MHz (max SM clock)"
+                                 f" / {SEG_INST} instructions per segment",
+                     "fwd_frac": nnz / (t_fwd * 1e-3) / 1e9 / seg_peak,
                      "sm_mhz_under_load": sm_mhz},
         "cpu_baseline": cpu,
         "precision_vs_fp64_oracle": prec,
@@ -516,11 +552,15 @@ def main():
         dist.destroy_process_group()
 
 
-# From the committed ncu capture of the backprojector on the 512^2/800-view
-# slice (profiles/): warp instructions and DRAM bytes per launch.  None until
-# captured for the current kernel.
-BWD_WARP_INST_512_V800 = 961_736_922
-BWD_DRAM_BYTES_512_V800 = 19_284_736
+# Thread-instructions of the least a segment evaluation takes (overlap
+# compare, intersection length, gather, FMA, loop step): the divisor of the
+# issue-limited peak.
+SEG_INST = 8
+# DRAM bytes (read + write) of one backprojector launch on the 512^2 / 800-view
+# slice, from the committed ncu capture of the current kernel (None when the
+# kernel has changed since).
+BWD_DRAM_BYTES_512_V800 = None
+
 
 if __name__ == "__main__":
     main()

@@ -55,7 +55,8 @@ typedef enum {
     AIR_ERR_CUDA = -3,         /* a CUDA runtime call failed */
     AIR_ERR_TIMEOUT = -4,      /* a bounded device-side wait gave up */
     AIR_ERR_BUDGET = -5,       /* request can never fit the server's HBM budget */
-    AIR_ERR_NOT_READY = -6     /* server request not finished yet */
+    AIR_ERR_NOT_READY = -6,    /* server request not finished yet */
+    AIR_ERR_INTERNAL = -7      /* a host-side consistency check of a plan's tables failed */
 } air_status;
 
 enum { AIR_FILTER_NONE = 0, AIR_FILTER_RAMLAK = 1 };

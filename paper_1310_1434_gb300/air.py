@@ -21,6 +21,7 @@ AIR_ERR_CUDA = -3
 AIR_ERR_TIMEOUT = -4
 AIR_ERR_BUDGET = -5
 AIR_ERR_NOT_READY = -6
+AIR_ERR_INTERNAL = -7
 FILTER_NONE, FILTER_RAMLAK = 0, 1
 PREC_FP32, PREC_BF16X3 = 0, 1
 

@@ -33,7 +33,7 @@ enum Op : int {
     OP_ZERO,       // x = 0, b = 0, g = 0, cg.stop = 0
     OP_FRAMELET,   // out = W in            (API call)
     OP_FRAMELET_T, // out = W^T in          (API call)
-    OP_TRANSPOSE,  // xt = transpose(src)   (before every OP_FWD; arg = FwdSrc)
+    OP_TRANSPOSE,  // xp, xt = padded src, transpose(src)   (before every OP_FWD; arg = FwdSrc)
     OP_BWD_FIN,    // sum the backprojector's view parts, then the BwdMode epilogue
     OP_COUNT
 };
@@ -85,7 +85,6 @@ struct SliceDesc {
     float dx;            // mm per pixel
     float inv_dgamma;    // 1 / bin pitch
     float jmid;          // (nb - 1) / 2
-    float half_k;        // bound factor of the backprojector's bin search (see bwd_pixel)
     int filter;          // AIR_FILTER_*
     // tables (plan-owned, read-only)
     const RayFx *ray;    // [V*nb] fixed-point rays
@@ -94,7 +93,7 @@ struct SliceDesc {
     float ramp_diag;     // taps[0] + 2 sum_{odd m < nb} taps[m]
     // solver state (plan-owned workspace)
     float *x, *r, *p, *q, *rhs0, *g;   // n*n
-    float *xt;                         // n*n: transposed copy of the projector's input
+    float *xp, *xt;                    // n*(n+2) each: zero-padded copy and transpose of the projector's input
     float *bwd_part;                   // bwd_parts * n*n: the backprojector's per-view-part sums
     int bwd_parts;                     // S: views split over S blocks per pixel tile (tuned)
     int fwd_vpb;                       // projector tile: views per block (1, 2, 4, 8; tuned)
@@ -126,9 +125,8 @@ __host__ __device__ inline int tiles_fwd(const SliceDesc &s) {
     return ((s.V + s.fwd_vpb - 1) / s.fwd_vpb) * ((s.nb + bpb - 1) / bpb);
 }
 __host__ __device__ inline int tiles_ramp(const SliceDesc &s) { return s.V; }
-// backprojector tile: 16 x 16 pixels x one of bwd_parts view parts; the
-// block's 256 threads are 16 view slots x 16 strip lanes
-constexpr int BWD_T = 16, BWD_SLOTS = AIR_THREADS / BWD_T, BWD_PAD = BWD_T + 1;
+// backprojector tile: 16 x 16 pixels x one of bwd_parts view parts
+constexpr int BWD_T = 16;
 __host__ __device__ inline int tiles_bwd_xy(const SliceDesc &s) {
     return ((s.n + BWD_T - 1) / BWD_T) * ((s.n + BWD_T - 1) / BWD_T);
 }

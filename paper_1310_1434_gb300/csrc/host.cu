@@ -100,7 +100,8 @@ size_t plan_bytes_estimate(const air_geometry &g) {
     const size_t nn = (size_t)g.n * g.n, rays = (size_t)g.n_views * g.n_bins;
     const size_t parts = (size_t)choose_bwd_parts(s);
     size_t b = rays * sizeof(RayFx) + (size_t)g.n_views * 16 + (size_t)g.n_bins * 4;
-    b += nn * 4 * (7 + parts + 18 + 1);          // x r p q rhs0 g xt, parts, b b2, xbuf
+    b += nn * 4 * (6 + 2 * parts + 18 + 1);      // x r p q rhs0 g, parts (up to 2x), b b2, xbuf
+    b += (size_t)g.n * (g.n + 2) * 4 * 2;        // xp xt
     b += rays * 4 * 3;                           // z zc ybuf
     b += sizeof(CgState) + ((size_t)max_reduce_tiles(s) + 64) * 8 + 24 * 256;
     if (g.precision == AIR_PREC_BF16X3) {
@@ -153,9 +154,10 @@ RayFx air::make_ray_fx(double px, double py, double ux, double uy, int n) {
         ks = floor_div(r.L0 - N2, Mp) + 1;                  // lo(k) < N2
         ke = ceil_div(r.L0 + (long long)r.Ma, Mp);          // hi(k) > 0
     }
-    if (ks < 0) ks = 0;
-    if (ke > n) ke = n;
-    if (ke < ks) ke = ks;
+    // clamp to [0, n] before packing: a ray that misses the image can give a
+    // start column far outside it (kk holds 16 bits per end)
+    ks = std::min<long long>(std::max<long long>(ks, 0), n);
+    ke = std::min<long long>(std::max<long long>(ke, ks), n);
     auto meets = [&](long long k) {
         const long long lo = r.L0 + k * M;
         return lo + (long long)r.Ma > 0 && lo < N2;
@@ -293,7 +295,8 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     const int parts_max = std::min(V, 2 * s.bwd_parts);
     // carve one allocation
     struct Piece { void **dst; size_t bytes; };
-    float *x, *r, *p, *q, *rhs0, *gg, *b, *b2, *z, *zc, *ybuf, *xbuf, *xt, *bpart;
+    float *x, *r, *p, *q, *rhs0, *gg, *b, *b2, *z, *zc, *ybuf, *xbuf, *xp, *xt, *bpart;
+    const size_t npad = (size_t)n * (n + 2);   // padded copies of the projector's input
     RayFx *ray;
     float4 *view;
     float *taps;
@@ -302,7 +305,7 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     const size_t npart = (size_t)max_reduce_tiles(s) + 64;
     std::vector<Piece> pieces = {
         {(void **)&ray, rays * sizeof(RayFx)}, {(void **)&view, (size_t)V * sizeof(float4)},
-        {(void **)&xt, nn * 4}, {(void **)&bpart, (size_t)parts_max * nn * 4},
+        {(void **)&xp, npad * 4}, {(void **)&xt, npad * 4}, {(void **)&bpart, (size_t)parts_max * nn * 4},
         {(void **)&taps, (size_t)nb * sizeof(float)},
         {(void **)&x, nn * 4}, {(void **)&r, nn * 4}, {(void **)&p, nn * 4}, {(void **)&q, nn * 4},
         {(void **)&rhs0, nn * 4}, {(void **)&gg, nn * 4}, {(void **)&b, 9 * nn * 4}, {(void **)&b2, 9 * nn * 4},
@@ -344,6 +347,22 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
             hray[(size_t)v * nb + j] = make_ray_fx(px, py, ux, uy, n);
         }
     }
+    // the projector walks [k0, k1) without bounds checks (the image copies
+    // it reads are padded by one entry per row end): every walked column must
+    // lie in the image and its span start in rows [-1, n-1]
+    for (const RayFx &r : hray) {
+        const int k0 = r.kk & 0xffff, k1 = r.kk >> 16;
+        bool ok = 0 <= k0 && k0 <= k1 && k1 <= n;
+        for (int k : {k0, k1 - 1}) {
+            if (!ok || k0 == k1) break;
+            const long long r0 = (r.L0 + (long long)k * r.M) >> 32;
+            ok = r0 >= -1 && r0 <= n - 1;
+        }
+        if (!ok) {
+            cudaFree(mem);
+            return fail(AIR_ERR_INTERNAL, "ray table: a walk range leaves the image");
+        }
+    }
     const double c0 = M_PI / ((double)V * g.pixel_mm * g.pixel_mm);
     double diag = 0.0;   // h[0] + 2 sum_{odd m < nb} h[m]: the difference form's centre weight
     for (int k = nb - 1; k >= 0; --k) {
@@ -352,13 +371,12 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
         diag += k == 0 ? h : 2.0 * h;
     }
     s.ramp_diag = (float)(c0 * diag);
-    // nearest approach of a pixel centre to a source, in pixels
-    const double l_min = (g.dso_mm - g.n * g.pixel_mm / std::sqrt(2.0)) / g.pixel_mm;
-    s.half_k = (float)(1.002 / (1.0 - 0.75 / l_min));
     cudaError_t e = cudaMemcpy(ray, hray.data(), rays * sizeof(RayFx), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(view, hview.data(), V * sizeof(float4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(taps, htaps.data(), nb * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(cg, 0, sizeof(CgState));
+    if (e == cudaSuccess) e = cudaMemset(xp, 0, npad * 4);   // the pads stay zero
+    if (e == cudaSuccess) e = cudaMemset(xt, 0, npad * 4);
     if (e != cudaSuccess) {
         cudaFree(mem);
         return fail(AIR_ERR_CUDA, std::string("plan table upload: ") + cudaGetErrorString(e));
@@ -366,7 +384,7 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     s.ray = ray;
     s.view = view;
     s.taps = taps;
-    s.x = x; s.r = r; s.p = p; s.q = q; s.rhs0 = rhs0; s.g = gg; s.b = b; s.b2 = b2; s.xt = xt;
+    s.x = x; s.r = r; s.p = p; s.q = q; s.rhs0 = rhs0; s.g = gg; s.b = b; s.b2 = b2; s.xp = xp; s.xt = xt;
     s.bwd_part = bpart;
     s.z = z; s.zc = zc; s.y = ybuf;
     s.cg = cg;

@@ -11,44 +11,44 @@ namespace air {
 // Forward projector A (Eq. 1): Y_{v,j} = dx * sum_i l_ij X_i, l_ij the exact
 // length of ray (v,j) inside pixel i.  Ray-driven, one thread per ray.  The
 // ray is walked along its major axis one column (row) at a time; in column k
-// its span [lo, lo + Ma] (fixed point, 2^-32 px) touches one or two pixel
-// rows, whose lengths are the integer overlaps times c (see RayFx).  A ray
-// walking columns reads the transposed image so that the 32 neighbouring
-// rays of a warp read neighbouring addresses.
+// its span [lo, lo + Ma] (fixed point, 2^-32 px) touches row r0 = lo >> 32
+// and, when the low word lo32 + Ma wraps past 2^32, row r0 + 1 too.  The
+// overlaps are ov1 = (lo32 + Ma) mod 2^32 with the next row (0 without a
+// wrap) and ov0 = Ma - ov1 with row r0, and the lengths ov * c (see RayFx).
+// The walk reads zero-padded copies of the image (entry -1 and n of every
+// row are zero, and r0 lies in [-1, n-1] on the walk range), so it needs no
+// bounds checks; rays walking columns read the transposed copy so that the
+// rays of a warp read neighbouring addresses.  The per-ray factor c is taken
+// out of the sum: a unit input still gives the entry ov * c exactly.
 // ======================================================================
-__device__ __forceinline__ float fx_len(unsigned ov, float c) {
-    return __fmul_rn(__uint2float_rn(ov), c);
-}
+__host__ __device__ inline int pad_ld(int n) { return n + 2; }   // row stride of the padded copies
 
-__device__ __forceinline__ float fx_ray(const float *__restrict__ X, const float *__restrict__ XT, int n,
+// sum over the walk of ov * X (without c), from the padded copies
+__device__ __forceinline__ float fx_ray(const float *__restrict__ XP, const float *__restrict__ XTP, int n,
                                         const RayFx &r) {
     const int k0 = r.kk & 0xffff, k1 = r.kk >> 16;
-    const float *__restrict__ src = r.o ? XT : X;     // row k of src = column (row) k of the walk
+    const int ld = pad_ld(n);
+    const float *__restrict__ row = (r.o ? XTP : XP) + (size_t)k0 * ld + 1;   // row k, entry 0
     const long long M = r.M;
     const unsigned Ma = r.Ma;
-    const float c = r.c;
     long long lo = r.L0 + (long long)k0 * M;
-    float acc = 0.f;
+    float a0 = 0.f, a1 = 0.f;
 #pragma unroll 2
     for (int k = k0; k < k1; ++k) {
-        const long long hi = lo + (long long)Ma;
         const int r0 = (int)(lo >> 32);
-        const int r1 = (int)((hi - 1) >> 32);
-        const bool two = r1 != r0;
-        // overlap with row r0 and (when the span crosses a row boundary) r1
-        const unsigned ov0 = two ? 0u - (unsigned)lo : Ma;
-        const unsigned ov1 = two ? (unsigned)hi : 0u;
-        const float *__restrict__ row = src + (size_t)k * n;
-        if ((unsigned)r0 < (unsigned)n) acc = fmaf(fx_len(ov0, c), __ldg(row + r0), acc);
-        if (two && (unsigned)r1 < (unsigned)n) acc = fmaf(fx_len(ov1, c), __ldg(row + r1), acc);
+        const unsigned t = (unsigned)lo + Ma;
+        const unsigned ov1 = t < Ma ? t : 0u;      // t < Ma iff the add wrapped
+        const unsigned ov0 = Ma - ov1;
+        a0 = fmaf(__uint2float_rn(ov0), __ldg(row + r0), a0);
+        if (ov1 != 0u) a1 = fmaf(__uint2float_rn(ov1), __ldg(row + r0 + 1), a1);
         lo += M;
+        row += ld;
     }
-    return acc;
+    return a0 + a1;
 }
 
 __device__ __forceinline__ void tile_fwd(const SliceDesc &s, int arg, int tile) {
     if (arg == SRC_P && s.cg->stop) return;
-    const float *src = arg == SRC_X ? s.x : (arg == SRC_P ? s.p : s.ext_in);
     float *dst = arg == SRC_EXT ? s.ext_out : s.z;
     // tile = (view group, bin range); a warp holds neighbouring bins of one
     // view, and the warps of a block neighbouring views, whose rays walk
@@ -60,23 +60,28 @@ __device__ __forceinline__ void tile_fwd(const SliceDesc &s, int arg, int tile) 
     if (v >= s.V || j >= s.nb) return;
     const int idx = v * s.nb + j;
     const RayFx r = s.ray[idx];
-    dst[idx] = s.dx * fx_ray(src, s.xt, s.n, r);
+    dst[idx] = s.dx * (r.c * fx_ray(s.xp, s.xt, s.n, r));
 }
 
-// xt = transpose(src), 32 x 32 tiles through shared memory (runs before
-// every projection: rays that walk columns read xt).
+// xp = src and xt = transpose(src), both zero-padded (row stride n + 2,
+// entry -1 at offset 0), in 32 x 32 tiles through shared memory; runs
+// before every projection.  The pads are zeroed once with the plan.
 __device__ __forceinline__ void tile_transpose(const SliceDesc &s, int arg, int tile, float *sm) {
     if (arg == SRC_P && s.cg->stop) return;
     const float *src = arg == SRC_X ? s.x : (arg == SRC_P ? s.p : s.ext_in);
-    const int n = s.n, tpr = (n + 31) / 32;
+    const int n = s.n, tpr = (n + 31) / 32, ld = pad_ld(n);
     const int x0 = (tile % tpr) * 32, y0 = (tile / tpr) * 32;
     float(*t)[33] = reinterpret_cast<float(*)[33]>(sm);
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     for (int yy = ty; yy < 32; yy += AIR_THREADS / 32)
-        if (y0 + yy < n && x0 + tx < n) t[yy][tx] = src[(size_t)(y0 + yy) * n + x0 + tx];
+        if (y0 + yy < n && x0 + tx < n) {
+            const float v = src[(size_t)(y0 + yy) * n + x0 + tx];
+            t[yy][tx] = v;
+            s.xp[(size_t)(y0 + yy) * ld + 1 + x0 + tx] = v;
+        }
     __syncthreads();
     for (int xx = ty; xx < 32; xx += AIR_THREADS / 32)
-        if (x0 + xx < n && y0 + tx < n) s.xt[(size_t)(x0 + xx) * n + y0 + tx] = t[tx][xx];
+        if (x0 + xx < n && y0 + tx < n) s.xt[(size_t)(x0 + xx) * ld + 1 + y0 + tx] = t[tx][xx];
     __syncthreads();
 }
 
@@ -107,15 +112,18 @@ __device__ __forceinline__ bool reduce_tiles(const SliceDesc &s, int tile, int n
 
 // ======================================================================
 // Backprojector A^T, the exact transpose of tile_fwd, without atomics.
-// A tile is a 16 x 16 block of pixels and one of S parts of the views.  The
-// block's threads are 16 view slots of 16 lanes: for each of its views a slot
-// sweeps every ray that can meet the tile, and lane c takes the tile's column
-// c for rays that walk columns and its row c for rays that walk rows.  There
-// the ray's span touches one or two pixels of the lane's strip, with the same
-// integer overlaps the projector computes, and the lane adds length * Z to
-// its own shared-memory accumulator of that pixel.  Each pixel's sum is
-// thereby formed in a fixed order by one lane per slot; the slots are then
-// summed in a fixed order, and the S parts by OP_BWD_FIN.
+// A tile is a 16 x 16 block of pixels and one of S parts of the views.  Each
+// warp takes whole views; for each it sweeps every ray that can meet the
+// tile, two rays at a time (half-warp h takes rays J0 + h, J0 + h + 2, ...).
+// Lane c of a half takes the tile's column c for rays that walk columns and
+// its row c for rays that walk rows; there the ray's span touches one or two
+// pixels of the lane's strip, with the same integer overlaps the projector
+// computes, and the lane adds ov * (c z) to its own shared-memory
+// accumulator of that pixel.  Accumulators are laid out [row][lane], so the
+// 32 lanes of a warp always hit 32 different banks, and have one padding row
+// on each side that catches spans just outside the tile (discarded).  Each
+// pixel's sum is formed in a fixed order by one lane per half-warp; the
+// halves are summed in a fixed order, and the S parts by OP_BWD_FIN.
 // ======================================================================
 // arctan(u) for |u| <= 0.45 by its Maclaurin (Gregory) series through u^13;
 // the alternating-series remainder is below 0.45^15/15 = 4.2e-7 rad, far
@@ -142,8 +150,11 @@ __device__ __forceinline__ float fan_angle(float4 w, float x, float y) {
     return fabsf(u) <= 0.45f ? atan_series(u) : atan2f(cr, dt);
 }
 
-// Shared memory of a backprojector tile: two [slots][lanes][16 + 1] arrays.
-constexpr int BWD_SMEM_FLOATS = 2 * BWD_SLOTS * BWD_T * BWD_PAD;
+constexpr int BWD_WARPS = AIR_THREADS / 32;
+constexpr int BWD_ROWS = BWD_T + 2;                 // rows -1 .. 16 of a strip
+constexpr int BWD_ORI = BWD_ROWS * 32;              // one orientation of one warp: [row][lane]
+// Shared memory of a backprojector tile: [warp][orientation][row][lane].
+constexpr int BWD_SMEM_FLOATS = BWD_WARPS * 2 * BWD_ORI;
 
 __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile, float *sm) {
     if (mode == BWD_Q && s.cg->stop) return;
@@ -151,56 +162,56 @@ __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile,
     const int ntxy = tiles_bwd_xy(s), part = tile / ntxy, txy = tile - part * ntxy;
     const int tpr = (n + BWD_T - 1) / BWD_T;
     const int X0 = (txy % tpr) * BWD_T, Y0 = (txy / tpr) * BWD_T;
-    float *accH = sm;                                  // [slot][column lane][row]
-    float *accV = sm + BWD_SLOTS * BWD_T * BWD_PAD;    // [slot][row lane][column]
     for (int i = threadIdx.x; i < BWD_SMEM_FLOATS; i += AIR_THREADS) sm[i] = 0.f;
     __syncthreads();
-    const int q = threadIdx.x / BWD_T, c = threadIdx.x % BWD_T;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int h = lane >> 4, c = lane & 15;
     const float *__restrict__ Z = mode == BWD_PLAIN ? s.ext_in : s.zc;
-    float *aH = accH + (q * BWD_T + c) * BWD_PAD;
-    float *aV = accV + (q * BWD_T + c) * BWD_PAD;
-    const int colk = X0 + c, rowk = Y0 + c;
-    const int nvH = min(BWD_T, n - Y0), nvV = min(BWD_T, n - X0);
-    // tile corners, pixel units, centred
-    const float xa = (float)X0 - s.half_n, xb = (float)min(X0 + BWD_T, n) - s.half_n;
-    const float ya = (float)Y0 - s.half_n, yb = (float)min(Y0 + BWD_T, n) - s.half_n;
+    // this lane's accumulator column: row i of orientation o at aH/aV + (i + 1) * 32
+    float *aH = sm + warp * 2 * BWD_ORI + lane;     // rays walking columns: [row][lane = column]
+    float *aV = aH + BWD_ORI;                       // rays walking rows:    [column][lane = row]
+    const int kH = X0 + c, kV = Y0 + c;
+    // the tile corner this lane evaluates (lanes 0..3 hold the four), pixel units, centred
+    const float cx = (float)((lane & 1) ? min(X0 + BWD_T, n) : X0) - s.half_n;
+    const float cy = (float)((lane & 2) ? min(Y0 + BWD_T, n) : Y0) - s.half_n;
     const int S = s.bwd_parts;
 #pragma unroll 1
-    for (int v = part + S * q; v < s.V; v += S * BWD_SLOTS) {
+    for (int v = part + S * warp; v < s.V; v += S * BWD_WARPS) {
         const float4 w = __ldg(s.view + v);
-        const float g0 = fan_angle(w, xa, ya), g1 = fan_angle(w, xb, ya);
-        const float g2 = fan_angle(w, xa, yb), g3 = fan_angle(w, xb, yb);
-        const float gmin = fminf(fminf(g0, g1), fminf(g2, g3)), gmax = fmaxf(fmaxf(g0, g1), fmaxf(g2, g3));
+        const float g = fan_angle(w, cx, cy);
+        const float g1 = __shfl_xor_sync(0xffffffffu, g, 1);
+        float gmin = fminf(g, g1), gmax = fmaxf(g, g1);
+        gmin = fminf(gmin, __shfl_xor_sync(0xffffffffu, gmin, 2));
+        gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, 2));
         const int J0 = max(0, (int)ceilf(fmaf(gmin, s.inv_dgamma, s.jmid) - 0.02f));
         const int J1 = min(nb - 1, (int)floorf(fmaf(gmax, s.inv_dgamma, s.jmid) + 0.02f));
         const RayFx *__restrict__ rr = s.ray + (size_t)v * nb;
         const float *__restrict__ zz = Z + (size_t)v * nb;
 #pragma unroll 2
-        for (int j = J0; j <= J1; ++j) {
+        for (int j = J0 + h; j <= J1; j += 2) {
             const RayFx r = rr[j];
-            const float z = __ldg(zz + j);
-            const int k = r.o ? colk : rowk;
-            const int base = r.o ? Y0 : X0;
-            const int nv = r.o ? nvH : nvV;
-            float *a = r.o ? aH : aV;
-            const long long lo = r.L0 + (long long)k * r.M;
-            const long long hi = lo + (long long)r.Ma;
-            const int r0 = (int)(lo >> 32);
-            const int r1 = (int)((hi - 1) >> 32);
-            const bool two = r1 != r0;
-            const unsigned ov0 = two ? 0u - (unsigned)lo : r.Ma;
-            const unsigned ov1 = two ? (unsigned)hi : 0u;
-            const int i0 = r0 - base, i1 = r1 - base;
-            if (k < n && (unsigned)i0 < (unsigned)nv) a[i0] = fmaf(fx_len(ov0, r.c), z, a[i0]);
-            if (k < n && two && (unsigned)i1 < (unsigned)nv) a[i1] = fmaf(fx_len(ov1, r.c), z, a[i1]);
+            const float cz = r.c * __ldg(zz + j);
+            const bool col = r.o != 0;
+            const long long lo = r.L0 + (long long)(col ? kH : kV) * r.M;
+            const int i0 = (int)(lo >> 32) - (col ? Y0 : X0);
+            const unsigned t = (unsigned)lo + r.Ma;
+            const unsigned ov1 = t < r.Ma ? t : 0u;
+            const unsigned ov0 = r.Ma - ov1;
+            if ((unsigned)(i0 + 1) < (unsigned)(BWD_T + 1)) {   // row i0 in [-1, 15]
+                float *a = (col ? aH : aV) + (i0 + 1) * 32;
+                a[0] = fmaf(__uint2float_rn(ov0), cz, a[0]);
+                if (ov1 != 0u) a[32] = fmaf(__uint2float_rn(ov1), cz, a[32]);
+            }
         }
     }
     __syncthreads();
     const int lx = threadIdx.x % BWD_T, ly = threadIdx.x / BWD_T;
     float acc = 0.f;
 #pragma unroll 4
-    for (int k = 0; k < BWD_SLOTS; ++k)
-        acc += accH[(k * BWD_T + lx) * BWD_PAD + ly] + accV[(k * BWD_T + ly) * BWD_PAD + lx];
+    for (int k = 0; k < BWD_WARPS * 2; ++k) {    // (warp, half) in a fixed order
+        const float *b = sm + (k >> 1) * 2 * BWD_ORI + (k & 1) * 16;
+        acc += b[(ly + 1) * 32 + lx] + b[BWD_ORI + (lx + 1) * 32 + ly];
+    }
     const int ix = X0 + lx, iy = Y0 + ly;
     if (ix < n && iy < n) {
         if (S == 1 && mode == BWD_PLAIN) s.ext_out[iy * n + ix] = s.dx * acc;
