@@ -67,14 +67,27 @@ struct CgState {
 // length inside pixel (k, row) is ov * c, ov the integer overlap of the span
 // with [row, row + 1), c = sec/|M|.  Integer arithmetic is exact, so every
 // kernel that evaluates a (ray, pixel) pair gets the same length, bit for bit.
+// The first 16 bytes hold all the backprojector reads: M (0 < |M| < 2^32) is
+// its low word Mlo with the high word given by the sign of cs = +-c.
 struct __align__(16) RayFx {
     long long L0;      // lower edge of the span in column (row) 0, 2^-32 px
-    long long M;       // slope * 2^32; 0 < |M| <= 2^32 - 1
-    float c;           // sec / |M|: length (px) per unit of overlap
+    unsigned Mlo;      // low word of M = slope * 2^32
+    float cs;          // c with the sign of M
     unsigned Ma;       // |M|
     int kk;            // walk range [kk & 0xffff, kk >> 16)
     int o;             // 1: walk columns (reads X^T), 0: walk rows (reads X)
+    int pad;
 };
+__host__ __device__ inline long long ray_M(const RayFx &r) {
+    return r.cs < 0.f ? (long long)r.Mlo - (1ll << 32) : (long long)r.Mlo;
+}
+
+// Per (view, backprojector pixel tile): the rays of the view that can meet
+// the tile, [J0, J1), and whether they all walk the same way.
+constexpr unsigned VT_MIXED = 1u << 29;   // the range holds both orientations
+__host__ __device__ inline unsigned vt_pack(int j0, int j1, int o, bool mixed) {
+    return (unsigned)j0 | ((unsigned)j1 << 14) | ((unsigned)o << 28) | (mixed ? VT_MIXED : 0u);
+}
 
 // Everything a tile function needs to know about one slice.  Plain data:
 // copied by value into kernel parameters or into a device task table.
@@ -83,12 +96,10 @@ struct SliceDesc {
     int n, V, nb;
     float half_n;        // n / 2
     float dx;            // mm per pixel
-    float inv_dgamma;    // 1 / bin pitch
-    float jmid;          // (nb - 1) / 2
     int filter;          // AIR_FILTER_*
     // tables (plan-owned, read-only)
     const RayFx *ray;    // [V*nb] fixed-point rays
-    const float4 *view;  // [V] {sx, sy, cx, cy}: source, unit central-ray direction
+    const unsigned *vt;  // [V][backprojector pixel tiles] ray ranges (vt_pack)
     const float *taps;   // [nb] c0 * h[k], k = 0..nb-1 (h even)
     float ramp_diag;     // taps[0] + 2 sum_{odd m < nb} taps[m]
     // solver state (plan-owned workspace)

@@ -99,7 +99,7 @@ size_t plan_bytes_estimate(const air_geometry &g) {
     s.nb = g.n_bins;
     const size_t nn = (size_t)g.n * g.n, rays = (size_t)g.n_views * g.n_bins;
     const size_t parts = (size_t)choose_bwd_parts(s);
-    size_t b = rays * sizeof(RayFx) + (size_t)g.n_views * 16 + (size_t)g.n_bins * 4;
+    size_t b = rays * sizeof(RayFx) + (size_t)g.n_views * tiles_bwd_xy(s) * 4 + (size_t)g.n_bins * 4;
     b += nn * 4 * (6 + 2 * parts + 18 + 1);      // x r p q rhs0 g, parts (up to 2x), b b2, xbuf
     b += (size_t)g.n * (g.n + 2) * 4 * 2;        // xp xt
     b += rays * 4 * 3;                           // z zc ybuf
@@ -138,10 +138,11 @@ RayFx air::make_ray_fx(double px, double py, double ux, double uy, int n) {
     if (M == 0) M = 1;        // an exactly axis-parallel ray, tilted by 2^-32
     const long long Y0 = std::llround(y0 * two32);
     RayFx r{};
-    r.M = M;
+    r.Mlo = (unsigned)(M & 0xffffffffll);
     r.L0 = Y0 + (M < 0 ? M : 0);
     r.Ma = (unsigned)(M < 0 ? -M : M);
-    r.c = (float)((1.0 / std::fabs(ua)) / (double)r.Ma);
+    const float c = (float)((1.0 / std::fabs(ua)) / (double)r.Ma);
+    r.cs = M < 0 ? -c : c;
     r.o = cols ? 1 : 0;
     // walk range: columns k in [0, n) whose span [lo, lo + Ma] meets rows [0, n)
     const long long N2 = (long long)n << 32;
@@ -285,8 +286,6 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     s.half_n = 0.5f * n;
     s.dx = (float)g.pixel_mm;
     const double dg = fan_pitch(g);
-    s.inv_dgamma = (float)(1.0 / dg);
-    s.jmid = 0.5f * (nb - 1);
     s.filter = g.filter;
 
     s.fwd_vpb = 1;
@@ -298,13 +297,14 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     float *x, *r, *p, *q, *rhs0, *gg, *b, *b2, *z, *zc, *ybuf, *xbuf, *xp, *xt, *bpart;
     const size_t npad = (size_t)n * (n + 2);   // padded copies of the projector's input
     RayFx *ray;
-    float4 *view;
+    unsigned *vt;
+    const int ntxy = tiles_bwd_xy(s);
     float *taps;
     CgState *cg;
     double *partial;
     const size_t npart = (size_t)max_reduce_tiles(s) + 64;
     std::vector<Piece> pieces = {
-        {(void **)&ray, rays * sizeof(RayFx)}, {(void **)&view, (size_t)V * sizeof(float4)},
+        {(void **)&ray, rays * sizeof(RayFx)}, {(void **)&vt, (size_t)V * ntxy * sizeof(unsigned)},
         {(void **)&xp, npad * 4}, {(void **)&xt, npad * 4}, {(void **)&bpart, (size_t)parts_max * nn * 4},
         {(void **)&taps, (size_t)nb * sizeof(float)},
         {(void **)&x, nn * 4}, {(void **)&r, nn * 4}, {(void **)&p, nn * 4}, {(void **)&q, nn * 4},
@@ -329,14 +329,14 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     // geometry tables, computed in FP64: per view the source (pixel units,
     // centred) and the central-ray direction; per ray the fixed-point line
     std::vector<RayFx> hray(rays);
-    std::vector<float4> hview(V);
+    std::vector<double4> hsrc(V);   // per view: source (pixel units, centred), central direction
     std::vector<float> htaps(nb);
     const double inv_dx = 1.0 / g.pixel_mm;
     for (int v = 0; v < V; ++v) {
         const double beta = g.beta0 + g.arc * (double)v / (double)V;
         const double cb = std::cos(beta), sb = std::sin(beta);
         const double Sx = g.dso_mm * cb, Sy = g.dso_mm * sb;
-        hview[v] = make_float4((float)(Sx * inv_dx), (float)(Sy * inv_dx), (float)(-cb), (float)(-sb));
+        hsrc[v] = make_double4(Sx * inv_dx, Sy * inv_dx, -cb, -sb);
         for (int j = 0; j < nb; ++j) {
             const double gamma = ((double)j - 0.5 * (nb - 1)) * dg;
             const double th = beta + M_PI + gamma;
@@ -355,12 +355,53 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
         bool ok = 0 <= k0 && k0 <= k1 && k1 <= n;
         for (int k : {k0, k1 - 1}) {
             if (!ok || k0 == k1) break;
-            const long long r0 = (r.L0 + (long long)k * r.M) >> 32;
+            const long long r0 = (r.L0 + (long long)k * ray_M(r)) >> 32;
             ok = r0 >= -1 && r0 <= n - 1;
         }
         if (!ok) {
             cudaFree(mem);
             return fail(AIR_ERR_INTERNAL, "ray table: a walk range leaves the image");
+        }
+    }
+    // backprojector ray ranges: per view and 16 x 16 pixel tile, the rays
+    // whose fan angle lies between the extreme fan angles of the tile's
+    // corners (the tile is convex and the source outside it, so exactly
+    // these rays can meet it), widened by 0.02 bin; and whether they all walk
+    // the same way.  Fan angles at the corner grid are shared by neighbouring
+    // tiles.
+    const int tpr = (n + BWD_T - 1) / BWD_T;
+    std::vector<unsigned> hvt((size_t)V * ntxy);
+    {
+        std::vector<double> gam((size_t)(tpr + 1) * (tpr + 1));
+        std::vector<int> chg(nb);   // number of orientation changes among rays 0..j
+        const double jm = 0.5 * (nb - 1);
+        for (int v = 0; v < V; ++v) {
+            const double4 w = hsrc[v];
+            for (int iy = 0; iy <= tpr; ++iy)
+                for (int ix = 0; ix <= tpr; ++ix) {
+                    const double px = std::min(ix * BWD_T, n) - 0.5 * n, py = std::min(iy * BWD_T, n) - 0.5 * n;
+                    const double dxs = px - w.x, dys = py - w.y;
+                    gam[(size_t)iy * (tpr + 1) + ix] = std::atan2(w.z * dys - w.w * dxs, w.z * dxs + w.w * dys);
+                }
+            const RayFx *rv = hray.data() + (size_t)v * nb;
+            chg[0] = 0;
+            for (int j = 1; j < nb; ++j) chg[j] = chg[j - 1] + (rv[j].o != rv[j - 1].o);
+            for (int ty = 0; ty < tpr; ++ty)
+                for (int tx = 0; tx < tpr; ++tx) {
+                    double gmin = 1e30, gmax = -1e30;
+                    for (int cy = 0; cy < 2; ++cy)
+                        for (int cx = 0; cx < 2; ++cx) {
+                            const double gc = gam[(size_t)(ty + cy) * (tpr + 1) + tx + cx];
+                            gmin = std::min(gmin, gc);
+                            gmax = std::max(gmax, gc);
+                        }
+                    const double f0 = std::ceil(gmin / dg + jm - 0.02), f1 = std::floor(gmax / dg + jm + 0.02);
+                    const int j0 = (int)std::max(0.0, std::min(f0, (double)nb));
+                    const int j1 = (int)std::max(-1.0, std::min(f1, (double)nb - 1));   // inclusive
+                    unsigned ent = vt_pack(0, 0, 0, false);
+                    if (j1 >= j0) ent = vt_pack(j0, j1 + 1, rv[j0].o, chg[j1] != chg[j0]);
+                    hvt[(size_t)v * ntxy + ty * tpr + tx] = ent;
+                }
         }
     }
     const double c0 = M_PI / ((double)V * g.pixel_mm * g.pixel_mm);
@@ -372,7 +413,7 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     }
     s.ramp_diag = (float)(c0 * diag);
     cudaError_t e = cudaMemcpy(ray, hray.data(), rays * sizeof(RayFx), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(view, hview.data(), V * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(vt, hvt.data(), hvt.size() * sizeof(unsigned), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(taps, htaps.data(), nb * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(cg, 0, sizeof(CgState));
     if (e == cudaSuccess) e = cudaMemset(xp, 0, npad * 4);   // the pads stay zero
@@ -382,7 +423,7 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
         return fail(AIR_ERR_CUDA, std::string("plan table upload: ") + cudaGetErrorString(e));
     }
     s.ray = ray;
-    s.view = view;
+    s.vt = vt;
     s.taps = taps;
     s.x = x; s.r = r; s.p = p; s.q = q; s.rhs0 = rhs0; s.g = gg; s.b = b; s.b2 = b2; s.xp = xp; s.xt = xt;
     s.bwd_part = bpart;

@@ -29,7 +29,7 @@ __device__ __forceinline__ float fx_ray(const float *__restrict__ XP, const floa
     const int k0 = r.kk & 0xffff, k1 = r.kk >> 16;
     const int ld = pad_ld(n);
     const float *__restrict__ row = (r.o ? XTP : XP) + (size_t)k0 * ld + 1;   // row k, entry 0
-    const long long M = r.M;
+    const long long M = ray_M(r);
     const unsigned Ma = r.Ma;
     long long lo = r.L0 + (long long)k0 * M;
     float a0 = 0.f, a1 = 0.f;
@@ -60,7 +60,7 @@ __device__ __forceinline__ void tile_fwd(const SliceDesc &s, int arg, int tile) 
     if (v >= s.V || j >= s.nb) return;
     const int idx = v * s.nb + j;
     const RayFx r = s.ray[idx];
-    dst[idx] = s.dx * (r.c * fx_ray(s.xp, s.xt, s.n, r));
+    dst[idx] = s.dx * (fabsf(r.cs) * fx_ray(s.xp, s.xt, s.n, r));
 }
 
 // xp = src and xt = transpose(src), both zero-padded (row stride n + 2,
@@ -113,48 +113,46 @@ __device__ __forceinline__ bool reduce_tiles(const SliceDesc &s, int tile, int n
 // ======================================================================
 // Backprojector A^T, the exact transpose of tile_fwd, without atomics.
 // A tile is a 16 x 16 block of pixels and one of S parts of the views.  Each
-// warp takes whole views; for each it sweeps every ray that can meet the
-// tile, two rays at a time (half-warp h takes rays J0 + h, J0 + h + 2, ...).
-// Lane c of a half takes the tile's column c for rays that walk columns and
-// its row c for rays that walk rows; there the ray's span touches one or two
-// pixels of the lane's strip, with the same integer overlaps the projector
-// computes, and the lane adds ov * (c z) to its own shared-memory
-// accumulator of that pixel.  Accumulators are laid out [row][lane], so the
-// 32 lanes of a warp always hit 32 different banks, and have one padding row
-// on each side that catches spans just outside the tile (discarded).  Each
-// pixel's sum is formed in a fixed order by one lane per half-warp; the
-// halves are summed in a fixed order, and the S parts by OP_BWD_FIN.
+// warp takes whole views; for each it sweeps the rays of the view that meet
+// the tile (a range the plan computes, see vt_pack), two rays at a time: half
+// h of the warp takes rays J0 + h, J0 + h + 2, ...  Lane c of a half takes
+// the tile's column c for rays that walk columns and its row c for rays that
+// walk rows; there the ray's span touches one or two pixels of the lane's
+// strip, with the same integer overlaps the projector computes, and the lane
+// adds ov * (c z) to its own shared-memory accumulator of that pixel.
+// Accumulators are laid out [row][lane], so the 32 lanes of a warp always hit
+// 32 different banks, and have one padding row on each side that catches
+// spans just outside the tile (discarded).  Each pixel's sum is formed in a
+// fixed order by one lane per half-warp; the halves are summed in a fixed
+// order, and the S parts by OP_BWD_FIN.
 // ======================================================================
-// arctan(u) for |u| <= 0.45 by its Maclaurin (Gregory) series through u^13;
-// the alternating-series remainder is below 0.45^15/15 = 4.2e-7 rad, far
-// inside the margin of the bin search below.
-__device__ __forceinline__ float atan_series(float u) {
-    const float w = u * u;
-    float p = 1.f / 13.f;
-    p = fmaf(p, w, -1.f / 11.f);
-    p = fmaf(p, w, 1.f / 9.f);
-    p = fmaf(p, w, -1.f / 7.f);
-    p = fmaf(p, w, 1.f / 5.f);
-    p = fmaf(p, w, -1.f / 3.f);
-    p = fmaf(p, w, 1.f);
-    return u * p;
-}
-
-// Fan angle of point (x, y) (pixel units, centred) seen from the source of
-// view w = {sx, sy, cx, cy}, measured from the central ray.
-__device__ __forceinline__ float fan_angle(float4 w, float x, float y) {
-    const float dxs = x - w.x, dys = y - w.y;
-    const float cr = w.z * dys - w.w * dxs;   // L sin(gamma)
-    const float dt = w.z * dxs + w.w * dys;   // L cos(gamma), > 0
-    const float u = __fdividef(cr, dt);
-    return fabsf(u) <= 0.45f ? atan_series(u) : atan2f(cr, dt);
-}
-
 constexpr int BWD_WARPS = AIR_THREADS / 32;
 constexpr int BWD_ROWS = BWD_T + 2;                 // rows -1 .. 16 of a strip
 constexpr int BWD_ORI = BWD_ROWS * 32;              // one orientation of one warp: [row][lane]
 // Shared memory of a backprojector tile: [warp][orientation][row][lane].
 constexpr int BWD_SMEM_FLOATS = BWD_WARPS * 2 * BWD_ORI;
+
+// One ray for one lane: k = the lane's column (row) of the walk, basem1 =
+// the tile's first row (column) - 1, a = the lane's accumulator column of
+// that orientation.  lo(k) = L0 + k M is formed as the 32 x 32 -> 64-bit
+// product k * Mlo plus L0, and k * (high word of M) added to the top.
+__device__ __forceinline__ void bwd_ray(const float4 q, float z, unsigned k, int basem1, float *a) {
+    const unsigned Mlo = __float_as_uint(q.z);
+    const int Mhi = __float_as_int(q.w) >> 31;                    // 0 or -1: the sign of M
+    const unsigned long long L0 = ((unsigned long long)__float_as_uint(q.y) << 32) | __float_as_uint(q.x);
+    const unsigned long long p = (unsigned long long)k * Mlo + L0;
+    const int row = (int)(unsigned)(p >> 32) + (int)k * Mhi - basem1;   // pixel row i0 + 1
+    const unsigned Ma = (Mlo ^ (unsigned)Mhi) - (unsigned)Mhi;     // |M|
+    const unsigned t = (unsigned)p + Ma;
+    const unsigned ov1 = t < Ma ? t : 0u;
+    const unsigned ov0 = Ma - ov1;
+    const float cz = fabsf(q.w) * z;
+    if ((unsigned)row < (unsigned)(BWD_T + 1)) {                 // i0 in [-1, 15]
+        float *ap = a + row * 32;
+        ap[0] = fmaf(__uint2float_rn(ov0), cz, ap[0]);
+        if (ov1 != 0u) ap[32] = fmaf(__uint2float_rn(ov1), cz, ap[32]);
+    }
+}
 
 __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile, float *sm) {
     if (mode == BWD_Q && s.cg->stop) return;
@@ -170,37 +168,29 @@ __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile,
     // this lane's accumulator column: row i of orientation o at aH/aV + (i + 1) * 32
     float *aH = sm + warp * 2 * BWD_ORI + lane;     // rays walking columns: [row][lane = column]
     float *aV = aH + BWD_ORI;                       // rays walking rows:    [column][lane = row]
-    const int kH = X0 + c, kV = Y0 + c;
-    // the tile corner this lane evaluates (lanes 0..3 hold the four), pixel units, centred
-    const float cx = (float)((lane & 1) ? min(X0 + BWD_T, n) : X0) - s.half_n;
-    const float cy = (float)((lane & 2) ? min(Y0 + BWD_T, n) : Y0) - s.half_n;
+    const unsigned kH = X0 + c, kV = Y0 + c;
     const int S = s.bwd_parts;
+    const unsigned *__restrict__ vt = s.vt + txy;
 #pragma unroll 1
     for (int v = part + S * warp; v < s.V; v += S * BWD_WARPS) {
-        const float4 w = __ldg(s.view + v);
-        const float g = fan_angle(w, cx, cy);
-        const float g1 = __shfl_xor_sync(0xffffffffu, g, 1);
-        float gmin = fminf(g, g1), gmax = fmaxf(g, g1);
-        gmin = fminf(gmin, __shfl_xor_sync(0xffffffffu, gmin, 2));
-        gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, 2));
-        const int J0 = max(0, (int)ceilf(fmaf(gmin, s.inv_dgamma, s.jmid) - 0.02f));
-        const int J1 = min(nb - 1, (int)floorf(fmaf(gmax, s.inv_dgamma, s.jmid) + 0.02f));
+        const unsigned e = __ldg(vt + (size_t)v * ntxy);
+        const int j0 = e & 0x3fff, j1 = (e >> 14) & 0x3fff;
         const RayFx *__restrict__ rr = s.ray + (size_t)v * nb;
         const float *__restrict__ zz = Z + (size_t)v * nb;
+        if (!(e & VT_MIXED)) {        // one orientation for the whole range (the usual case)
+            const bool col = (e >> 28) & 1u;
+            const unsigned k = col ? kH : kV;
+            const int basem1 = (col ? Y0 : X0) - 1;
+            float *a = col ? aH : aV;
 #pragma unroll 2
-        for (int j = J0 + h; j <= J1; j += 2) {
-            const RayFx r = rr[j];
-            const float cz = r.c * __ldg(zz + j);
-            const bool col = r.o != 0;
-            const long long lo = r.L0 + (long long)(col ? kH : kV) * r.M;
-            const int i0 = (int)(lo >> 32) - (col ? Y0 : X0);
-            const unsigned t = (unsigned)lo + r.Ma;
-            const unsigned ov1 = t < r.Ma ? t : 0u;
-            const unsigned ov0 = r.Ma - ov1;
-            if ((unsigned)(i0 + 1) < (unsigned)(BWD_T + 1)) {   // row i0 in [-1, 15]
-                float *a = (col ? aH : aV) + (i0 + 1) * 32;
-                a[0] = fmaf(__uint2float_rn(ov0), cz, a[0]);
-                if (ov1 != 0u) a[32] = fmaf(__uint2float_rn(ov1), cz, a[32]);
+            for (int j = j0 + h; j < j1; j += 2)
+                bwd_ray(__ldg(reinterpret_cast<const float4 *>(rr + j)), __ldg(zz + j), k, basem1, a);
+        } else {
+#pragma unroll 1
+            for (int j = j0 + h; j < j1; j += 2) {
+                const bool col = rr[j].o != 0;
+                bwd_ray(__ldg(reinterpret_cast<const float4 *>(rr + j)), __ldg(zz + j), col ? kH : kV,
+                        (col ? Y0 : X0) - 1, col ? aH : aV);
             }
         }
     }
