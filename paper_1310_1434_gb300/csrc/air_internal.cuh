@@ -99,7 +99,7 @@ struct SliceDesc {
     int filter;          // AIR_FILTER_*
     // tables (plan-owned, read-only)
     const RayFx *ray;    // [V*nb] fixed-point rays
-    const unsigned *vt;  // [V][backprojector pixel tiles] ray ranges (vt_pack)
+    const unsigned *vt;  // [backprojector pixel tile][V] ray ranges (vt_pack)
     const float *taps;   // [nb] c0 * h[k], k = 0..nb-1 (h even)
     float ramp_diag;     // taps[0] + 2 sum_{odd m < nb} taps[m]
     // solver state (plan-owned workspace)

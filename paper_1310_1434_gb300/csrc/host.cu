@@ -400,7 +400,7 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
                     const int j1 = (int)std::max(-1.0, std::min(f1, (double)nb - 1));   // inclusive
                     unsigned ent = vt_pack(0, 0, 0, false);
                     if (j1 >= j0) ent = vt_pack(j0, j1 + 1, rv[j0].o, chg[j1] != chg[j0]);
-                    hvt[(size_t)v * ntxy + ty * tpr + tx] = ent;
+                    hvt[(size_t)(ty * tpr + tx) * V + v] = ent;
                 }
         }
     }

@@ -129,34 +129,35 @@ __device__ __forceinline__ bool reduce_tiles(const SliceDesc &s, int tile, int n
 constexpr int BWD_WARPS = AIR_THREADS / 32;
 constexpr int BWD_ROWS = BWD_T + 2;                 // rows -1 .. 16 of a strip
 constexpr int BWD_ORI = BWD_ROWS * 32;              // one orientation of one warp: [row][lane]
-// Shared memory of a backprojector tile: [warp][orientation][row][lane].
-constexpr int BWD_SMEM_FLOATS = BWD_WARPS * 2 * BWD_ORI;
+constexpr int BWD_CHUNK = 32;                       // rays a warp stages at a time
+// per warp: accumulators [orientation][row][lane], then the staged rays as
+// two float4 per ray
+constexpr int BWD_WARP_FLOATS = 2 * BWD_ORI + 2 * 4 * BWD_CHUNK;
+constexpr int BWD_SMEM_FLOATS = BWD_WARPS * BWD_WARP_FLOATS;
 
-// One ray for one lane: k = the lane's column (row) of the walk, basem1 =
-// the tile's first row (column) - 1, a = the lane's accumulator column of
-// that orientation.  lo(k) = L0 + k M is formed as the 32 x 32 -> 64-bit
-// product k * Mlo plus L0, and k * (high word of M) added to the top.
-__device__ __forceinline__ void bwd_ray(const float4 q, float z, unsigned k, int basem1, float *a) {
-    const unsigned Mlo = __float_as_uint(q.z);
-    const int Mhi = __float_as_int(q.w) >> 31;                    // 0 or -1: the sign of M
-    const unsigned long long L0 = ((unsigned long long)__float_as_uint(q.y) << 32) | __float_as_uint(q.x);
-    const unsigned long long p = (unsigned long long)k * Mlo + L0;
-    const int row = (int)(unsigned)(p >> 32) + (int)k * Mhi - basem1;   // pixel row i0 + 1
-    const unsigned Ma = (Mlo ^ (unsigned)Mhi) - (unsigned)Mhi;     // |M|
+// A staged ray, relative to the tile: {L0 - (base - 1) 2^32 as two words,
+// Mlo, |M|} and {c z, high word of M, orientation}.  Lane k of the walk
+// (the tile's column or row) finds its span at lo = L0' + k M, formed as
+// the 32 x 32 -> 64-bit product k * Mlo plus L0', with k * (high word of M)
+// added to the top: the top word is then the pixel row i0 + 1 in the strip.
+__device__ __forceinline__ void bwd_ray(const float4 A, const float4 B, unsigned k, float *a) {
+    const unsigned long long L0 = ((unsigned long long)__float_as_uint(A.y) << 32) | __float_as_uint(A.x);
+    const unsigned long long p = (unsigned long long)k * __float_as_uint(A.z) + L0;
+    const int row = (int)(unsigned)(p >> 32) + (int)k * __float_as_int(B.y);
+    const unsigned Ma = __float_as_uint(A.w);
     const unsigned t = (unsigned)p + Ma;
-    const unsigned ov1 = t < Ma ? t : 0u;
+    const unsigned ov1 = t < Ma ? t : 0u;          // t < Ma iff the add wrapped: the span enters row i0 + 1
     const unsigned ov0 = Ma - ov1;
-    const float cz = fabsf(q.w) * z;
-    if ((unsigned)row < (unsigned)(BWD_T + 1)) {                 // i0 in [-1, 15]
+    if ((unsigned)row < (unsigned)(BWD_T + 1)) {   // i0 in [-1, 15]
         float *ap = a + row * 32;
-        ap[0] = fmaf(__uint2float_rn(ov0), cz, ap[0]);
-        if (ov1 != 0u) ap[32] = fmaf(__uint2float_rn(ov1), cz, ap[32]);
+        ap[0] = fmaf(__uint2float_rn(ov0), B.x, ap[0]);
+        if (ov1 != 0u) ap[32] = fmaf(__uint2float_rn(ov1), B.x, ap[32]);
     }
 }
 
 __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile, float *sm) {
     if (mode == BWD_Q && s.cg->stop) return;
-    const int n = s.n, nb = s.nb;
+    const int n = s.n, nb = s.nb, V = s.V;
     const int ntxy = tiles_bwd_xy(s), part = tile / ntxy, txy = tile - part * ntxy;
     const int tpr = (n + BWD_T - 1) / BWD_T;
     const int X0 = (txy % tpr) * BWD_T, Y0 = (txy / tpr) * BWD_T;
@@ -165,41 +166,81 @@ __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int h = lane >> 4, c = lane & 15;
     const float *__restrict__ Z = mode == BWD_PLAIN ? s.ext_in : s.zc;
+    float *wsm = sm + warp * BWD_WARP_FLOATS;
     // this lane's accumulator column: row i of orientation o at aH/aV + (i + 1) * 32
-    float *aH = sm + warp * 2 * BWD_ORI + lane;     // rays walking columns: [row][lane = column]
+    float *aH = wsm + lane;                         // rays walking columns: [row][lane = column]
     float *aV = aH + BWD_ORI;                       // rays walking rows:    [column][lane = row]
+    float4 *stA = reinterpret_cast<float4 *>(wsm + 2 * BWD_ORI);
+    float4 *stB = stA + BWD_CHUNK;
     const unsigned kH = X0 + c, kV = Y0 + c;
-    const int S = s.bwd_parts;
-    const unsigned *__restrict__ vt = s.vt + txy;
-#pragma unroll 1
-    for (int v = part + S * warp; v < s.V; v += S * BWD_WARPS) {
-        const unsigned e = __ldg(vt + (size_t)v * ntxy);
-        const int j0 = e & 0x3fff, j1 = (e >> 14) & 0x3fff;
-        const RayFx *__restrict__ rr = s.ray + (size_t)v * nb;
-        const float *__restrict__ zz = Z + (size_t)v * nb;
-        if (!(e & VT_MIXED)) {        // one orientation for the whole range (the usual case)
-            const bool col = (e >> 28) & 1u;
-            const unsigned k = col ? kH : kV;
-            const int basem1 = (col ? Y0 : X0) - 1;
-            float *a = col ? aH : aV;
-#pragma unroll 2
-            for (int j = j0 + h; j < j1; j += 2)
-                bwd_ray(__ldg(reinterpret_cast<const float4 *>(rr + j)), __ldg(zz + j), k, basem1, a);
-        } else {
-#pragma unroll 1
-            for (int j = j0 + h; j < j1; j += 2) {
-                const bool col = rr[j].o != 0;
-                bwd_ray(__ldg(reinterpret_cast<const float4 *>(rr + j)), __ldg(zz + j), col ? kH : kV,
-                        (col ? Y0 : X0) - 1, col ? aH : aV);
-            }
+    const int S = s.bwd_parts, dv = S * BWD_WARPS;
+    const unsigned *__restrict__ vtt = s.vt + (size_t)txy * V;     // this tile's entries, by view
+
+    // ray j of view v into registers (lane = position in the chunk)
+    float4 rq = make_float4(0.f, 0.f, 0.f, 0.f);
+    float rz = 0.f;
+    int ro = 0;
+    auto fetch = [&](unsigned e, int v, int j) {
+        if (j < (int)((e >> 14) & 0x3fffu)) {
+            const RayFx *rp = s.ray + (size_t)v * nb + j;
+            rq = __ldg(reinterpret_cast<const float4 *>(rp));
+            rz = __ldg(Z + (size_t)v * nb + j);
+            if (e & VT_MIXED) ro = rp->o;
         }
+    };
+    int v = part + S * warp;
+    unsigned e = v < V ? __ldg(vtt + v) : 0u;
+    unsigned en = v + dv < V ? __ldg(vtt + v + dv) : 0u;
+    if (v < V) fetch(e, v, (int)(e & 0x3fffu) + lane);
+#pragma unroll 1
+    for (; v < V; v += dv) {
+        const int vn = v + dv;
+        const unsigned enn = vn + dv < V ? __ldg(vtt + vn + dv) : 0u;   // two views ahead
+        const int j0 = e & 0x3fffu, j1 = (e >> 14) & 0x3fffu;
+        const bool mixed = (e & VT_MIXED) != 0u, colv = ((e >> 28) & 1u) != 0u;
+        if (j0 >= j1 && vn < V) fetch(en, vn, (int)(en & 0x3fffu) + lane);
+#pragma unroll 1
+        for (int c0 = j0; c0 < j1; c0 += BWD_CHUNK) {
+            if (c0 != j0) fetch(e, v, c0 + lane);                       // ranges longer than a chunk
+            {   // stage this lane's ray, tile-relative
+                const bool col = mixed ? ro != 0 : colv;
+                const long long basem1 = (long long)((col ? Y0 : X0) - 1);
+                const unsigned long long L0 =
+                    (((unsigned long long)__float_as_uint(rq.y) << 32) | __float_as_uint(rq.x)) -
+                    ((unsigned long long)basem1 << 32);
+                const unsigned Mlo = __float_as_uint(rq.z);
+                const int Mhi = __float_as_int(rq.w) >> 31;
+                stA[lane] = make_float4(__uint_as_float((unsigned)L0), __uint_as_float((unsigned)(L0 >> 32)),
+                                        rq.z, __uint_as_float((Mlo ^ (unsigned)Mhi) - (unsigned)Mhi));
+                stB[lane] = make_float4(fabsf(rq.w) * rz, __int_as_float(Mhi), __int_as_float((int)col), 0.f);
+            }
+            __syncwarp();
+            const int cnt = min(BWD_CHUNK, j1 - c0);
+            if (c0 + BWD_CHUNK >= j1 && vn < V) fetch(en, vn, (int)(en & 0x3fffu) + lane);   // next view
+            if (!mixed) {
+                const unsigned k = colv ? kH : kV;
+                float *a = colv ? aH : aV;
+#pragma unroll 2
+                for (int i = h; i < cnt; i += 2) bwd_ray(stA[i], stB[i], k, a);
+            } else {
+#pragma unroll 1
+                for (int i = h; i < cnt; i += 2) {
+                    const float4 B = stB[i];
+                    const bool col = __float_as_int(B.z) != 0;
+                    bwd_ray(stA[i], B, col ? kH : kV, col ? aH : aV);
+                }
+            }
+            __syncwarp();
+        }
+        e = en;
+        en = enn;
     }
     __syncthreads();
     const int lx = threadIdx.x % BWD_T, ly = threadIdx.x / BWD_T;
     float acc = 0.f;
 #pragma unroll 4
     for (int k = 0; k < BWD_WARPS * 2; ++k) {    // (warp, half) in a fixed order
-        const float *b = sm + (k >> 1) * 2 * BWD_ORI + (k & 1) * 16;
+        const float *b = sm + (k >> 1) * BWD_WARP_FLOATS + (k & 1) * 16;
         acc += b[(ly + 1) * 32 + lx] + b[BWD_ORI + (lx + 1) * 32 + ly];
     }
     const int ix = X0 + lx, iy = Y0 + ly;
