@@ -245,18 +245,21 @@ air_status autotune(air_plan *P) {
             best_vpb = vpb;
         }
     }
-    // backprojector: view split around the heuristic's choice
+    // backprojector: view splits up to the part buffer's size, timed as the
+    // solver runs them (the parts, then their sum, OP_BWD_FIN, which the CG
+    // epilogue needs at any split); the heuristic's choice is tried first
+    // and kept unless another is 2 % faster
     t = s;
-    t.ext_in = s.z;
-    t.ext_out = s.r;
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.zc, 0, (size_t)s.V * s.nb * 4, st);
     const int S0 = s.bwd_parts;
     int best_S = S0;
     best = 1e30f;
-    for (int S : {S0, std::max(1, S0 / 4), std::max(1, S0 / 2), std::min(P->bwd_parts_max, 2 * S0)}) {
+    for (int S : {S0, 1, 2, 3, 4, 6, 8, 12, 16}) {
+        if (S > P->bwd_parts_max || (S == S0 && best < 1e30f)) continue;
         t.bwd_parts = S;
         const float ms = timed([&] {
-            if (e == cudaSuccess) e = launch_op(OP_BWD, t, BWD_PLAIN, st);
-            if (e == cudaSuccess && S > 1) e = launch_op(OP_BWD_FIN, t, BWD_PLAIN, st);
+            if (e == cudaSuccess) e = launch_op(OP_BWD, t, BWD_RHS0, st);
+            if (e == cudaSuccess) e = launch_op(OP_BWD_FIN, t, BWD_RHS0, st);
         });
         if (ms < best * 0.98f) {
             best = ms;
