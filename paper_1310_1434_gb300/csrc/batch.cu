@@ -24,9 +24,15 @@ using namespace air;
 
 namespace {
 
+// Side streams the tensor-core filters of one phase fork onto during capture
+// (each slice's filter is a small GEMM that fills part of the GPU alone).
+constexpr int TC_SIDE = 8;
+
 struct BatchGraph {
     std::vector<uintptr_t> key;
     cudaStream_t cap = nullptr;     // private stream the graph is captured on
+    cudaStream_t side[TC_SIDE] = {};
+    cudaEvent_t fork = nullptr, join[TC_SIDE] = {};
     cudaGraphExec_t exec = nullptr;
     char *dmem = nullptr;
     BatchCtl *ctl = nullptr;
@@ -39,9 +45,24 @@ BatchGraph g_grouped, g_persistent;
 void release(BatchGraph &b) {
     if (b.exec) cudaGraphExecDestroy(b.exec);
     if (b.dmem) cudaFree(b.dmem);
-    cudaStream_t cap = b.cap;
-    b = BatchGraph();
-    b.cap = cap;
+    BatchGraph keep;   // the capture streams and events outlive a graph
+    keep.cap = b.cap;
+    keep.fork = b.fork;
+    for (int i = 0; i < TC_SIDE; ++i) {
+        keep.side[i] = b.side[i];
+        keep.join[i] = b.join[i];
+    }
+    b = keep;
+}
+
+cudaError_t make_side_streams(BatchGraph &b) {
+    cudaError_t e = cudaSuccess;
+    if (!b.fork) e = cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming);
+    for (int i = 0; i < TC_SIDE && e == cudaSuccess; ++i) {
+        if (!b.side[i]) e = cudaStreamCreateWithFlags(&b.side[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess && !b.join[i]) e = cudaEventCreateWithFlags(&b.join[i], cudaEventDisableTiming);
+    }
+    return e;
 }
 
 struct Batch {
@@ -170,6 +191,7 @@ extern "C" air_status air_solve_batch(int n, air_plan *const *plans, const float
         // captured on a private stream (the caller's may be the legacy default
         // stream, which cannot be captured); launched on the caller's stream
         if (e == cudaSuccess && !G.cap) e = cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = make_side_streams(G);
         if (e == cudaSuccess) e = cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) {
             release(G);
@@ -177,23 +199,43 @@ extern "C" air_status air_solve_batch(int n, air_plan *const *plans, const float
         }
         const cudaStream_t cs = G.cap;
         cudaError_t le = cudaSuccess;
-        for (const Launch &L : launches) {
-            if (L.op == OP_RAMP_TC) {
-                const SliceDesc &sd = B.slices[L.slice];
-                const float *src = L.arg == RSRC_Y ? sd.y : sd.z;
-                if (ramp_tc_apply(plans[L.slice], src, sd.zc, sd.cg, L.arg == RSRC_Z, cs) != AIR_OK) {
-                    const std::string msg = air_last_error();
-                    cudaGraph_t g = nullptr;
-                    cudaStreamEndCapture(cs, &g);
-                    if (g) cudaGraphDestroy(g);
-                    release(G);
-                    cudaGetLastError();
-                    return fail(AIR_ERR_CUDA, "batch graph build: " + msg);
-                }
-            } else {
+        std::string tc_msg;
+        for (size_t li = 0; li < launches.size() && le == cudaSuccess && tc_msg.empty(); ++li) {
+            const Launch &L = launches[li];
+            if (L.op != OP_RAMP_TC) {
                 le = launch_group(L.op, d_slices, d_tasks + L.off, L.ntasks, L.tiles, L.smem, cs);
-                if (le != cudaSuccess) break;
+                continue;
             }
+            // a run of tensor-core filters (one phase, one per BF16X3 slice):
+            // fork them onto the side streams and join them back
+            size_t end = li;
+            while (end < launches.size() && launches[end].op == OP_RAMP_TC &&
+                   (end == li || launches[end].slice > launches[end - 1].slice))
+                ++end;
+            const int nside = (int)std::min<size_t>(TC_SIDE, end - li);
+            le = cudaEventRecord(G.fork, cs);
+            for (int k = 0; k < nside && le == cudaSuccess; ++k) le = cudaStreamWaitEvent(G.side[k], G.fork, 0);
+            for (size_t q = li; q < end && le == cudaSuccess && tc_msg.empty(); ++q) {
+                const Launch &T = launches[q];
+                const SliceDesc &sd = B.slices[T.slice];
+                const float *src = T.arg == RSRC_Y ? sd.y : sd.z;
+                if (ramp_tc_apply(plans[T.slice], src, sd.zc, sd.cg, T.arg == RSRC_Z, G.side[(q - li) % TC_SIDE]) !=
+                    AIR_OK)
+                    tc_msg = air_last_error();
+            }
+            for (int k = 0; k < nside && le == cudaSuccess; ++k) {
+                le = cudaEventRecord(G.join[k], G.side[k]);
+                if (le == cudaSuccess) le = cudaStreamWaitEvent(cs, G.join[k], 0);
+            }
+            li = end - 1;
+        }
+        if (!tc_msg.empty()) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(cs, &g);
+            if (g) cudaGraphDestroy(g);
+            release(G);
+            cudaGetLastError();
+            return fail(AIR_ERR_CUDA, "batch graph build: " + tc_msg);
         }
         if ((s = end_capture(G, cs, le)) != AIR_OK) return s;
         G.key = B.key;
