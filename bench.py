@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--impl", default="air", choices=["air", "reference"])
     ap.add_argument("--batch", type=int, default=8, help="slices per step (even: half 800, half 200 views)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", default=None, choices=["fwd", "bwd", "ramp", "shrink", "solve", "plain", "batch"],
+    ap.add_argument("--kernel", default=None,
+                    choices=["fwd", "bwd", "ramp", "ramp_tc", "shrink", "solve", "plain", "batch"],
                     help="profiling mode: run one operator on the 512^2/800-view slice --reps times")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--serve-requests", type=int, default=24,
@@ -145,6 +146,9 @@ def run_kernel(args):
            "shrink": lambda: air.air_shrink(plan, Xd, b, gg, w.lam / w.mu),
            "solve": lambda: air.air_solve(plan, Yd, w.lam, w.mu, w.n_outer, w.n_cg, X2),
            "plain": lambda: air.air_solve(plan, Yd, w.lam, w.mu, 1, 2, X2)}
+    if args.kernel == "ramp_tc":   # the split-BF16 tensor-core filter
+        plan_tc = air.Plan(dataclasses.replace(g, precision=1))
+        ops["ramp_tc"] = lambda: air.air_filter(plan_tc, Yd, Zd)
     if args.kernel == "batch":   # the timed step: one batch as bench times it
         ws = workloads(max(2, args.batch), 0)
         Ys = [torch.as_tensor(inputs.make_case(v)[2].astype(np.float32).ravel(), device="cuda") for v in ws]
