@@ -162,6 +162,15 @@ def run_kernel(args):
     print(f"ran {args.kernel} x{args.reps}")
 
 
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of per-rank times over all ranks (a no-op alone)."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
 def workloads(batch: int, rank: int):
     out = []
     for i in range(batch):
@@ -487,10 +496,7 @@ def main():
     sm_mhz = clk.get("sm_mhz") or peaks["sm_max_mhz"]
 
     # ---- reduce over ranks (max time) ----
-    t_rank = torch.tensor([total_ms, float(np.sum(e2e_ms))], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
-    total_ms, e2e_total = float(t_rank[0]), float(t_rank[1])
+    total_ms, e2e_total = max_over_ranks([total_ms, float(np.sum(e2e_ms))], dist, dev)
     slices = B * args.steps * world
     value = slices / (total_ms / 1000.0)
     e2e_value = slices / (e2e_total / 1000.0)
