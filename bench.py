@@ -463,6 +463,30 @@ def main():
             lat[w.geom.n_views].append(t)
     plain_ms = [t for v in lat.values() for t in v]
 
+    # ---- the next rows: L2-regularised AIR (Eq. 5) and forward-backward
+    # splitting AIR (Eq. 6), single slice, 240 operator pairs each (as the
+    # 30 x 8 split-Bregman solve) ----
+    n_pairs = ws[0].n_outer * ws[0].n_cg
+    xl = torch.randn(ws[0].geom.n ** 2, device=dev)
+    xl /= xl.norm()
+    xl2 = torch.empty_like(xl)
+    yl = torch.empty(ws[0].geom.n_views * ws[0].geom.n_bins, device=dev)
+    lip = 1.0
+    for _ in range(10):   # power iteration for ||A'^T A||; the forward-backward step is its inverse
+        air.air_project(plans32[0], xl, yl)
+        air.air_filtered_backproject(plans32[0], yl, xl2)
+        lip = float(xl2.norm())
+        xl = xl2 / lip
+    step = 1.0 / lip
+    next_rows = {"slice": "512^2 / 800 views", "operator_pairs": n_pairs, "fbs_step": step}
+    for tag, pl in (("fp32", plans32[0]), ("bf16x3", plans[0])):
+        t_l2 = events_time(torch, stream, lambda: air.air_solve_l2(pl, Yd[0], ws[0].lam * 100, n_pairs, Xd[0]), 2)
+        t_fbs = events_time(torch, stream, lambda: air.air_solve_fbs(pl, Yd[0], ws[0].lam, step, n_pairs, Xd[0]), 2)
+        next_rows[f"l2_air_ms_{tag}"] = t_l2
+        next_rows[f"fbs_air_ms_{tag}"] = t_fbs
+    next_rows["l2_lambda"] = ws[0].lam * 100
+    next_rows["fbs_lambda"] = ws[0].lam
+
     # ---- dominant kernel: the backprojector on a 512^2/800 slice ----
     p800 = plans32[0]
     g8 = ws[0].geom
@@ -537,6 +561,7 @@ def main():
                       "ms_800_views": float(np.mean(lat[800])) if lat[800] else None,
                       "ms_200_views": float(np.mean(lat[200])) if lat[200] else None},
         "serving": serving,
+        "next_rows": next_rows,
         "latency_batch": {"p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
                           "note": "every slice of a batch completes with the batch"},
         "projector": {"fwd_ms": t_fwd, "bwd_ms": t_bwd, "alg_bytes": alg_bytes,

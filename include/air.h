@@ -176,6 +176,24 @@ AIR_API air_status air_shrink(const air_plan *plan, const float *X, float *b, fl
 AIR_API air_status air_solve(const air_plan *plan, const float *Y, float lambda, float mu,
                      int n_outer, int n_cg, float *X, double *resid, air_stream stream);
 
+/* L2-regularised AIR, Eq. (5): (A'^T A + lambda I) X = A'^T Y, A'^T = A^T C,
+ * solved by n_cg conjugate-gradient steps from X = 0 (CG dots in FP64 on the
+ * device).  Y: n_views*n_bins (input), X: n*n (output only).  lambda > 0,
+ * 0 <= n_cg <= 100000.  Uses the plan's filter and precision. */
+AIR_API air_status air_solve_l2(const air_plan *plan, const float *Y, float lambda, int n_cg, float *X,
+                                air_stream stream);
+
+/* Forward-backward splitting AIR (Methods, Eq. 6, the paper's ref. [25]) for
+ *   min_X 1/2 ||P (A X - Y)||^2 + lambda ||W X||_1:
+ *   X^0 = 0; for k < n_iter:
+ *     X^{k+1/2} = X^k - step A'^T (A X^k - Y)            (Eq. 6)
+ *     X^{k+1}   = W^T S_{step*lambda}(W X^{k+1/2})        (proximal step)
+ * with S the soft threshold on the high-pass bands 1..8 (band 0 kept) and W
+ * the tensor framelet (W^T W = I).  Y: n_views*n_bins, X: n*n (output only).
+ * lambda >= 0, step > 0, 0 <= n_iter <= 100000. */
+AIR_API air_status air_solve_fbs(const air_plan *plan, const float *Y, float lambda, float step, int n_iter,
+                                 float *X, air_stream stream);
+
 /* air_solve from and to HOST memory: copies Y_host in, solves, copies X out
  * and synchronises the stream before returning.  Y_host/X_host may be
  * pageable or pinned. */

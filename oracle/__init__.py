@@ -11,7 +11,10 @@ computes, written from the paper's definitions and sharing no code with it:
   Ram-Lak, linear convolution) and A'^T = A^T C of Eq. (5);
 * ``framelet`` / ``framelet_adjoint`` / ``shrink``: the tensor framelet W and
   the split-Bregman d/b update;
-* ``cg`` / ``solve``: the CG-solved L2 step and the split-Bregman loop.
+* ``cg`` / ``solve``: the CG-solved L2 step and the split-Bregman loop;
+* ``l2_solve`` / ``fbs``: L2-regularised AIR (Eq. 5) and forward-backward
+  splitting AIR (Eq. 6 plus the framelet proximal step), in numpy over the
+  functions above.
 
 Pins against the paper and the mathematics live in ``tests/test_oracle_*.py``.
 Parity of the full-size configurations beyond those pins is "parity
@@ -246,3 +249,28 @@ def solve(g, Y, lam: float, mu: float, n_outer: int, n_cg: int, return_resid=Fal
     r = np.zeros(max(n_outer, 1))
     _load().orc_solve(ctypes.byref(cg_), _dptr(Y), lam, mu, n_outer, n_cg, _dptr(X), _dptr(r))
     return (X, r[:n_outer]) if return_resid else X
+
+
+def l2_solve(g, Y, lam: float, n_cg: int) -> np.ndarray:
+    """L2-regularised AIR, Eq. (5): (A'^T A + lam I) X = A'^T Y with
+    A'^T = A^T C, by n_cg conjugate-gradient steps from X = 0."""
+    return cg(g, filtered_backproject(g, Y), lam, n_cg)
+
+
+def fbs(g, Y, lam: float, step: float, n_iter: int) -> np.ndarray:
+    """Forward-backward splitting AIR (Methods, Eq. 6) for
+    min 1/2 ||P(AX - Y)||^2 + lam ||W X||_1 from X = 0:
+      X_half = X - step A'^T (A X - Y)                      (Eq. 6)
+      X      = W^T S(W X_half),  S = soft threshold step * lam on the
+               high-pass bands 1..8, band 0 unchanged (the proximal step with
+               the tight frame W, W^T W = I)."""
+    cg_ = _geom(g)
+    Y = _f64(Y).reshape(cg_.n_views, cg_.n_bins)
+    X = np.zeros((cg_.n, cg_.n))
+    t = step * lam
+    for _ in range(n_iter):
+        Xh = X - step * filtered_backproject(g, project(g, X) - Y)
+        c = framelet(Xh)
+        c[1:] = np.sign(c[1:]) * np.maximum(np.abs(c[1:]) - t, 0.0)
+        X = framelet_adjoint(c)
+    return X

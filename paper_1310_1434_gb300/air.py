@@ -31,7 +31,7 @@ EXPORTS = ["air_last_error", "air_plan_create", "air_plan_destroy", "air_plan_by
            "air_project",
            "air_filter", "air_backproject", "air_filtered_backproject", "air_filtered_backproject_noalloc",
            "air_framelet", "air_shrink",
-           "air_solve", "air_solve_host", "air_solve_batch", "air_solve_batch_persistent", "air_server_create", "air_server_submit",
+           "air_solve", "air_solve_l2", "air_solve_fbs", "air_solve_host", "air_solve_batch", "air_solve_batch_persistent", "air_server_create", "air_server_submit",
            "air_server_poll", "air_server_wait", "air_server_times", "air_server_destroy"]
 
 
@@ -86,6 +86,8 @@ def load(build_if_missing: bool = False):
         "air_shrink": (i32, [P, P, P, P, f32, P, P]),
         "air_solve": (i32, [P, P, f32, f32, i32, i32, P, P, P]),
         "air_solve_host": (i32, [P, P, f32, f32, i32, i32, P, P]),
+        "air_solve_l2": (i32, [P, P, f32, i32, P, P]),
+        "air_solve_fbs": (i32, [P, P, f32, f32, i32, P, P]),
         "air_solve_batch": (i32, [i32, P, P, P, P, P, P, P, P]),
         "air_solve_batch_persistent": (i32, [i32, P, P, P, P, P, P, P, P]),
         "air_server_create": (i32, [ctypes.c_size_t, i32, ctypes.POINTER(P)]),
@@ -244,6 +246,16 @@ def air_shrink(plan: Plan, X, b, g, thresh: float, resid=None, stream=None):
 def air_solve(plan: Plan, Y, lam: float, mu: float, n_outer: int, n_cg: int, X, resid=None, stream=None):
     _check(load().air_solve(plan.handle, _ptr(Y), float(lam), float(mu), int(n_outer), int(n_cg), _ptr(X),
                             _ptr(resid), _stream(stream)), "air_solve")
+
+
+def air_solve_l2(plan: Plan, Y, lam: float, n_cg: int, X, stream=None):
+    _check(load().air_solve_l2(plan.handle, _ptr(Y), float(lam), int(n_cg), _ptr(X), _stream(stream)),
+           "air_solve_l2")
+
+
+def air_solve_fbs(plan: Plan, Y, lam: float, step: float, n_iter: int, X, stream=None):
+    _check(load().air_solve_fbs(plan.handle, _ptr(Y), float(lam), float(step), int(n_iter), _ptr(X),
+                                _stream(stream)), "air_solve_fbs")
 
 
 def air_solve_host(plan: Plan, Y_host, lam: float, mu: float, n_outer: int, n_cg: int, X_host, stream=None):

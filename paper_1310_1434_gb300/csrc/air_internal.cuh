@@ -35,6 +35,8 @@ enum Op : int {
     OP_FRAMELET_T, // out = W^T in          (API call)
     OP_TRANSPOSE,  // xp, xt = padded src, transpose(src)   (before every OP_FWD; arg = FwdSrc)
     OP_BWD_FIN,    // sum the backprojector's view parts, then the BwdMode epilogue
+    OP_AXPY,       // q = x + step r            (forward step of Eq. 6, r = A'^T(Y - A x))
+    OP_PROX,       // x = W^T S_tau(W q)        (framelet proximal step)
     OP_COUNT
 };
 
@@ -111,7 +113,8 @@ struct SliceDesc {
     float *b, *b2;                     // 9*n*n each (Bregman variable, double-buffered)
     float *z, *zc;                     // V*nb
     const float *y;                    // V*nb measured sinogram
-    float mu, tau;                     // mu, lambda/mu
+    float mu, tau;                     // mu, lambda/mu (forward-backward: 0, step * lambda)
+    float step;                        // forward-backward step size (Eq. 6)
     CgState *cg;
     double *partial;                   // per-tile partial sums (>= max reducing tiles)
     double *resid_out;                 // n_outer doubles or nullptr
@@ -155,8 +158,8 @@ __host__ __device__ inline int tiles_of(const SliceDesc &s, int op) {
     case OP_FWD: return tiles_fwd(s);
     case OP_RAMP: return tiles_ramp(s);
     case OP_BWD: return tiles_bwd(s);
-    case OP_CG_A: case OP_CG_B: case OP_ZERO: case OP_BWD_FIN: return tiles_vec(s);
-    case OP_SHRINK: case OP_FRAMELET: case OP_FRAMELET_T: case OP_TRANSPOSE: return tiles_shr(s);
+    case OP_CG_A: case OP_CG_B: case OP_ZERO: case OP_BWD_FIN: case OP_AXPY: return tiles_vec(s);
+    case OP_SHRINK: case OP_FRAMELET: case OP_FRAMELET_T: case OP_TRANSPOSE: case OP_PROX: return tiles_shr(s);
     default: return 0;
     }
 }

@@ -664,6 +664,37 @@ std::vector<Phase> solve_program(int n_outer, int n_cg, bool tc_ramp) {
     return prog;
 }
 
+// L2-regularised AIR, Eq. (5): (A'^T A + lambda I) X = A'^T Y by n_cg CG steps
+// from X = 0 (the first L2 step of the split-Bregman program with g = 0 and
+// mu = lambda, without the shrink).
+std::vector<Phase> l2_program(int n_cg, bool tc_ramp) {
+    std::vector<Phase> prog = solve_program(1, n_cg, tc_ramp);
+    prog.pop_back();   // the SHRINK of the outer step
+    return prog;
+}
+
+// Forward-backward splitting AIR: per iteration the forward step of Eq. (6),
+// X + step A'^T (Y - A X) (the residual epilogue at mu = 0 gives
+// r = A'^T Y - A'^T A X), then the framelet proximal step.
+std::vector<Phase> fbs_program(int n_iter, bool tc_ramp) {
+    std::vector<Phase> prog;
+    const int ramp = tc_ramp ? OP_RAMP_TC : OP_RAMP;
+    prog.push_back({ramp, RSRC_Y});
+    prog.push_back({OP_BWD, BWD_RHS0});
+    prog.push_back({OP_BWD_FIN, BWD_RHS0});
+    prog.push_back({OP_ZERO, 0});
+    for (int k = 0; k < n_iter; ++k) {
+        prog.push_back({OP_TRANSPOSE, SRC_X});
+        prog.push_back({OP_FWD, SRC_X});
+        prog.push_back({ramp, RSRC_Z});
+        prog.push_back({OP_BWD, BWD_RESID});
+        prog.push_back({OP_BWD_FIN, BWD_RESID});
+        prog.push_back({OP_AXPY, 0});
+        prog.push_back({OP_PROX, 0});
+    }
+    return prog;
+}
+
 air_status run_program_single(const air_plan *P, const SliceDesc &s, const std::vector<Phase> &prog,
                               cudaStream_t st) {
     for (const Phase &ph : prog) {
@@ -710,6 +741,31 @@ extern "C" air_status air_solve(const air_plan *P, const float *Y, float lambda,
     const bool tc = P->geom.precision == AIR_PREC_BF16X3 && P->geom.filter == AIR_FILTER_RAMLAK;
     SliceDesc s = solve_desc(P, Y, lambda, mu, X, resid);
     return run_program_single(P, s, solve_program(n_outer, n_cg, tc), (cudaStream_t)stream);
+}
+
+extern "C" air_status air_solve_l2(const air_plan *P, const float *Y, float lambda, int n_cg, float *X,
+                                   air_stream stream) {
+    if (!(lambda > 0.f) || !std::isfinite(lambda)) return fail(AIR_ERR_INVALID_ARG, "lambda must be > 0");
+    TRY(check_solve_args(P, Y, 0.f, lambda, 0, n_cg, X));
+    TRY(check_dev_ptr(Y, "Y"));
+    TRY(check_dev_ptr(X, "X"));
+    const bool tc = P->geom.precision == AIR_PREC_BF16X3 && P->geom.filter == AIR_FILTER_RAMLAK;
+    SliceDesc s = solve_desc(P, Y, 0.f, lambda, X, nullptr);
+    return run_program_single(P, s, l2_program(n_cg, tc), (cudaStream_t)stream);
+}
+
+extern "C" air_status air_solve_fbs(const air_plan *P, const float *Y, float lambda, float step, int n_iter,
+                                    float *X, air_stream stream) {
+    if (!(step > 0.f) || !std::isfinite(step)) return fail(AIR_ERR_INVALID_ARG, "step must be > 0");
+    TRY(check_solve_args(P, Y, lambda, 1.f, n_iter, 0, X));
+    TRY(check_dev_ptr(Y, "Y"));
+    TRY(check_dev_ptr(X, "X"));
+    const bool tc = P->geom.precision == AIR_PREC_BF16X3 && P->geom.filter == AIR_FILTER_RAMLAK;
+    SliceDesc s = solve_desc(P, Y, 0.f, 1.f, X, nullptr);
+    s.mu = 0.f;                 // the residual epilogue then gives A'^T (Y - A X)
+    s.tau = step * lambda;      // the proximal threshold
+    s.step = step;
+    return run_program_single(P, s, fbs_program(n_iter, tc), (cudaStream_t)stream);
 }
 
 extern "C" air_status air_solve_host(const air_plan *P, const float *Y_host, float lambda, float mu,

@@ -29,6 +29,8 @@ bool overlap(const void *a, size_t na, const void *b, size_t nb);
 size_t align_up(size_t v, size_t a);
 double fan_pitch(const air_geometry &g);
 std::vector<Phase> solve_program(int n_outer, int n_cg, bool tc_ramp);
+std::vector<Phase> l2_program(int n_cg, bool tc_ramp);
+std::vector<Phase> fbs_program(int n_iter, bool tc_ramp);
 air_status check_solve_args(const air_plan *P, const float *Y, float lambda, float mu, int n_outer,
                             int n_cg, const float *X);
 SliceDesc solve_desc(const air_plan *P, const float *Y, float lambda, float mu, float *X, double *resid);

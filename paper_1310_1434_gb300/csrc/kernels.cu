@@ -26,6 +26,10 @@ __global__ void __launch_bounds__(AIR_THREADS) k_op(const SliceDesc s, int arg) 
         tile_cg_b(s, tile);
     } else if constexpr (OP == OP_ZERO) {
         tile_zero(s, tile);
+    } else if constexpr (OP == OP_AXPY) {
+        tile_axpy(s, tile);
+    } else if constexpr (OP == OP_PROX) {
+        tile_prox(s, tile, sm);
     } else if constexpr (OP == OP_SHRINK) {
         if (arg < 2) {
             ShrinkArgs a{s.x, arg ? s.b2 : s.b, arg ? s.b : s.b2, s.g, s.tau};
@@ -70,6 +74,8 @@ cudaError_t launch_op(int op, const SliceDesc &s, int arg, cudaStream_t st) {
     case OP_FRAMELET_T: return launch_one<OP_FRAMELET>(s, 1, st);
     case OP_TRANSPOSE: return launch_one<OP_TRANSPOSE>(s, arg, st);
     case OP_BWD_FIN: return launch_one<OP_BWD_FIN>(s, arg, st);
+    case OP_AXPY: return launch_one<OP_AXPY>(s, arg, st);
+    case OP_PROX: return launch_one<OP_PROX>(s, arg, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -135,6 +141,8 @@ k_group(const SliceDesc *__restrict__ slices, const Task *__restrict__ tasks, in
     else if constexpr (OP == OP_CG_A) tile_cg_a(s, tile);
     else if constexpr (OP == OP_CG_B) tile_cg_b(s, tile);
     else if constexpr (OP == OP_ZERO) tile_zero(s, tile);
+    else if constexpr (OP == OP_AXPY) tile_axpy(s, tile);
+    else if constexpr (OP == OP_PROX) tile_prox(s, tile, sm);
     else if constexpr (OP == OP_TRANSPOSE) tile_transpose(s, t.arg, tile, sm);
     else if constexpr (OP == OP_SHRINK) {
         ShrinkArgs a{s.x, t.arg ? s.b2 : s.b, t.arg ? s.b : s.b2, s.g, s.tau};
@@ -168,6 +176,8 @@ cudaError_t launch_group(int op, const SliceDesc *d_slices, const Task *d_tasks,
     case OP_ZERO: return launch_group_op<OP_ZERO>(d_slices, d_tasks, ntasks, total_tiles, smem, st);
     case OP_TRANSPOSE: return launch_group_op<OP_TRANSPOSE>(d_slices, d_tasks, ntasks, total_tiles, smem, st);
     case OP_SHRINK: return launch_group_op<OP_SHRINK>(d_slices, d_tasks, ntasks, total_tiles, smem, st);
+    case OP_AXPY: return launch_group_op<OP_AXPY>(d_slices, d_tasks, ntasks, total_tiles, smem, st);
+    case OP_PROX: return launch_group_op<OP_PROX>(d_slices, d_tasks, ntasks, total_tiles, smem, st);
     default: return cudaErrorInvalidValue;
     }
 }

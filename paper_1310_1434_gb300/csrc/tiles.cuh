@@ -416,6 +416,18 @@ __device__ __forceinline__ void tile_cg_b(const SliceDesc &s, int tile) {
     }
 }
 
+// q = x + step r: the forward step of forward-backward splitting (Eq. 6),
+// with r = A'^T (Y - A x) from the OP_BWD_FIN residual epilogue at mu = 0.
+__device__ __forceinline__ void tile_axpy(const SliceDesc &s, int tile) {
+    const int nn = s.n * s.n;
+    const int base = tile * VEC_PER_TILE;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = base + k * AIR_THREADS + threadIdx.x;
+        if (i < nn) s.q[i] = fmaf(s.step, s.r[i], s.x[i]);
+    }
+}
+
 __device__ __forceinline__ void tile_zero(const SliceDesc &s, int tile) {
     const int nn = s.n * s.n;
     const int base = tile * VEC_PER_TILE;
@@ -579,6 +591,61 @@ __device__ __forceinline__ void tile_shrink(const SliceDesc &s, const ShrinkArgs
     __syncthreads();
 }
 
+// The proximal step of forward-backward splitting for R = ||W X||_1 with the
+// tight frame W (W^T W = I): x = W^T S_tau(W q), the high-pass bands
+// soft-thresholded by tau = step * lambda and the low-pass band kept.  Reads q
+// (with a 2-pixel periodic halo) and writes x, so tiles never read what
+// another tile writes.
+__device__ __forceinline__ void tile_prox(const SliceDesc &s, int tile, float *sm) {
+    const int n = s.n;
+    const int tpr = (n + SHR_T - 1) / SHR_T;
+    const int x0 = (tile % tpr) * SHR_T, y0 = (tile / tpr) * SHR_T;
+    float *Xs = sm;                      // [SHR_X][SHR_X], origin (y0-2, x0-2)
+    float *E = sm + SHR_X * SHR_X;       // [9][SHR_H][SHR_H], origin (y0-1, x0-1)
+    for (int k = threadIdx.x; k < SHR_X * SHR_X; k += AIR_THREADS) {
+        const int ly = k / SHR_X, lx = k % SHR_X;
+        Xs[k] = s.q[wrapi(y0 - 2 + ly, n) * n + wrapi(x0 - 2 + lx, n)];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < SHR_H * SHR_H; k += AIR_THREADS) {
+        const int cy = k / SHR_H, cx = k % SHR_H;
+        float nb3[3][3];
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) nb3[p][q] = Xs[(cy + p) * SHR_X + cx + q];
+        float wx[9];
+        framelet9(nb3, wx);
+#pragma unroll
+        for (int band = 0; band < 9; ++band) {
+            float d = wx[band];
+            if (band > 0) {
+                const float m = fabsf(d) - s.tau;
+                d = m > 0.f ? copysignf(m, d) : 0.f;
+            }
+            E[band * SHR_H * SHR_H + k] = d;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < SHR_T * SHR_T; k += AIR_THREADS) {
+        const int ly = k / SHR_T, lx = k % SHR_T;
+        if (y0 + ly >= n || x0 + lx >= n) continue;
+        float acc = 0.f;
+#pragma unroll
+        for (int band = 0; band < 9; ++band) {
+            float e3[3][3];
+            const float *Eb = E + band * SHR_H * SHR_H;
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) e3[p][q] = Eb[(ly + p) * SHR_H + lx + q];
+            acc += framelet_t1(band / 3, band % 3, e3);
+        }
+        s.x[(size_t)(y0 + ly) * n + x0 + lx] = acc;
+    }
+    __syncthreads();
+}
+
 // out = W in (adjoint = 0) or W^T in (adjoint = 1), for the API call.
 __device__ __forceinline__ void tile_framelet(const SliceDesc &s, int adjoint, int tile, float *sm) {
     const int n = s.n, nn = n * n;
@@ -627,7 +694,7 @@ __device__ __forceinline__ void tile_framelet(const SliceDesc &s, int adjoint, i
 __host__ inline size_t tile_smem(const SliceDesc &s, int op) {
     switch (op) {
     case OP_RAMP: return sizeof(float) * (4 * (size_t)s.nb + 2 * RAMP_R + 4);
-    case OP_SHRINK: return sizeof(float) * SHR_SMEM_FLOATS;
+    case OP_SHRINK: case OP_PROX: return sizeof(float) * SHR_SMEM_FLOATS;
     case OP_FRAMELET: case OP_FRAMELET_T: return sizeof(float) * 9 * SHR_H * SHR_H;
     case OP_TRANSPOSE: return sizeof(float) * 32 * 33;
     case OP_BWD: return sizeof(float) * BWD_SMEM_FLOATS;
@@ -646,6 +713,8 @@ __device__ __forceinline__ void run_tile(const SliceDesc &s, int op, int arg, in
     case OP_CG_A: tile_cg_a(s, tile); break;
     case OP_CG_B: tile_cg_b(s, tile); break;
     case OP_ZERO: tile_zero(s, tile); break;
+    case OP_AXPY: tile_axpy(s, tile); break;
+    case OP_PROX: tile_prox(s, tile, sm); break;
     case OP_SHRINK: {   // arg = parity of the outer step: b -> b2, then b2 -> b
         ShrinkArgs a{s.x, arg ? s.b2 : s.b, arg ? s.b : s.b2, s.g, s.tau};
         tile_shrink(s, a, tile, true, nullptr, sm);

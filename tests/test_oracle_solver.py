@@ -112,3 +112,61 @@ def test_split_bregman_matches_primal_dual(mats, filt):
     assert np.count_nonzero(np.abs((W @ Xcp)[N8 * N8:]) < 1e-9) > 5
     # ... and the split constraint d = W X is met in the limit
     assert resid[-1] <= 1e-6 * max(resid[0], 1e-30) + 1e-12
+
+
+# ---------------------------------------------- Eq. (5) and Eq. (6) ----
+def test_l2_solve_is_eq5_dense_solution(mats):
+    """Enough CG steps solve Eq. (5) exactly: (A^T C A + lam I) X = A^T C Y."""
+    g = small_geom()
+    A, C = mats[1]
+    Y = np.random.Generator(np.random.PCG64(11)).standard_normal((V8, B8))
+    lam = 0.3
+    ref = np.linalg.solve(A.T @ C @ A + lam * np.eye(N8 * N8), A.T @ C @ Y.ravel())
+    X = oracle.l2_solve(g, Y, lam, 200)
+    assert np.linalg.norm(X.ravel() - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_fbs_without_regulariser_converges_to_least_squares(mats):
+    """lam = 0 makes the proximal step the identity (W^T W = I), so Eq. (6)
+    is gradient descent on 1/2 ||P(AX - Y)||^2 and converges, for a step below
+    2 / ||A^T C A||, to the least-squares solution A^T C A X = A^T C Y."""
+    g = small_geom()
+    A, C = mats[1]
+    M = A.T @ C @ A
+    L = np.linalg.eigvalsh(M).max()
+    Y = (A @ smooth_truth().ravel()).reshape(V8, B8)
+    ref = np.linalg.lstsq(M, A.T @ C @ Y.ravel(), rcond=None)[0]
+    X = oracle.fbs(g, Y, 0.0, 1.0 / L, 4000)
+    # the component in M's null space stays at its start value, 0, as in lstsq
+    assert np.linalg.norm(X.ravel() - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+def test_fbs_infinite_threshold_is_the_framelet_lowpass_blur():
+    """A threshold above every coefficient zeroes the high-pass bands, so one
+    step from X = 0 gives W^T P_0 W X_half with X_half = step A'^T Y: the
+    periodic separable blur with (h0 * h0~) = [1, 4, 6, 4, 1] / 16 per axis."""
+    g = small_geom()
+    Y = np.random.Generator(np.random.PCG64(12)).standard_normal((V8, B8))
+    step = 0.7
+    X = oracle.fbs(g, Y, 1e30, step, 1)
+    Xh = step * oracle.filtered_backproject(g, Y)
+    k = np.array([1.0, 4.0, 6.0, 4.0, 1.0]) / 16.0
+    blur = sum(k[i] * np.roll(Xh, i - 2, axis=0) for i in range(5))
+    blur = sum(k[i] * np.roll(blur, i - 2, axis=1) for i in range(5))
+    assert np.allclose(X, blur, rtol=0, atol=1e-12 * np.abs(Xh).max())
+
+
+def test_fbs_threshold_scales_with_the_step():
+    """From X = 0 one iteration is X1 = W^T S_{step lam}(step W A'^T Y)
+    = step W^T S_lam(W A'^T Y) (soft thresholding is positively homogeneous),
+    so X1 / step does not depend on the step when the threshold is step * lam
+    (it would with a threshold of lam alone)."""
+    g = small_geom()
+    Y = np.random.Generator(np.random.PCG64(13)).standard_normal((V8, B8))
+    lam = 0.5 * np.abs(oracle.framelet(oracle.filtered_backproject(g, Y))[1:]).mean()
+    a = oracle.fbs(g, Y, lam, 0.5, 1) / 0.5
+    b = oracle.fbs(g, Y, lam, 2.0, 1) / 2.0
+    assert np.allclose(a, b, rtol=0, atol=1e-12 * np.abs(a).max())
+    # and the threshold is active: some but not all high-pass coefficients vanish
+    c = oracle.framelet(oracle.filtered_backproject(g, Y))[1:]
+    assert 0 < np.count_nonzero(np.abs(c) <= lam) < c.size
