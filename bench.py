@@ -484,6 +484,9 @@ def main():
         t_fbs = events_time(torch, stream, lambda: air.air_solve_fbs(pl, Yd[0], ws[0].lam, step, n_pairs, Xd[0]), 2)
         next_rows[f"l2_air_ms_{tag}"] = t_l2
         next_rows[f"fbs_air_ms_{tag}"] = t_fbs
+    xf = torch.empty_like(Xd[0])
+    air.air_fbp(plans32[0], Yd[0], xf)
+    next_rows["fbp_ms"] = events_time(torch, stream, lambda: air.air_fbp(plans32[0], Yd[0], xf), 5)
     next_rows["l2_lambda"] = ws[0].lam * 100
     next_rows["fbs_lambda"] = ws[0].lam
 

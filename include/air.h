@@ -194,6 +194,19 @@ AIR_API air_status air_solve_l2(const air_plan *plan, const float *Y, float lamb
 AIR_API air_status air_solve_fbs(const air_plan *plan, const float *Y, float lambda, float step, int n_iter,
                                  float *X, air_stream stream);
 
+/* Fan-beam filtered backprojection, the analytic reconstruction the paper
+ * compares AIR with (Materials: "FBP was used as the AR method"), by the
+ * textbook equiangular algorithm for a full 2 pi scan:
+ *   Q_v(j)  = alpha sum_k D cos(gamma_k) Y_v(k) g((j-k) alpha),
+ *             g(0) = 1/(8 alpha^2), g(odd m) = -1/(2 pi^2 sin^2(m alpha)), g(even) = 0;
+ *   X(x, y) = dbeta sum_v Q_v(gamma') / L^2   (gamma', L: fan angle and
+ *             source distance of the pixel centre; Q linear between bins,
+ *             zero beyond the detector; dbeta = 2 pi / n_views).
+ * alpha = fan pitch, D = dso_mm.  Y: n_views*n_bins (input), X: n*n (output),
+ * in the units of Y per mm.  AIR_ERR_INVALID_ARG unless the plan's arc is
+ * 2 pi.  FP32 whatever the plan's precision; uses the plan's workspace. */
+AIR_API air_status air_fbp(const air_plan *plan, const float *Y, float *X, air_stream stream);
+
 /* air_solve from and to HOST memory: copies Y_host in, solves, copies X out
  * and synchronises the stream before returning.  Y_host/X_host may be
  * pageable or pinned. */

@@ -14,7 +14,9 @@ computes, written from the paper's definitions and sharing no code with it:
 * ``cg`` / ``solve``: the CG-solved L2 step and the split-Bregman loop;
 * ``l2_solve`` / ``fbs``: L2-regularised AIR (Eq. 5) and forward-backward
   splitting AIR (Eq. 6 plus the framelet proximal step), in numpy over the
-  functions above.
+  functions above;
+* ``fbp``: the analytic reconstruction the paper compares against (FBP,
+  Materials), the textbook equiangular fan-beam algorithm, in numpy.
 
 Pins against the paper and the mathematics live in ``tests/test_oracle_*.py``.
 Parity of the full-size configurations beyond those pins is "parity
@@ -274,3 +276,72 @@ def fbs(g, Y, lam: float, step: float, n_iter: int) -> np.ndarray:
         c[1:] = np.sign(c[1:]) * np.maximum(np.abs(c[1:]) - t, 0.0)
         X = framelet_adjoint(c)
     return X
+
+
+def fbp_taps(g) -> np.ndarray:
+    """The equiangular fan-beam ramp g(m alpha), m = 0 .. n_bins-1 (alpha the
+    fan pitch): 1/(8 alpha^2) at 0, 0 at even m, -1/(2 pi^2 sin^2(m alpha)) at
+    odd m -- the band-limited ramp h(m alpha) times (1/2)(m alpha/sin m alpha)^2."""
+    cg_ = _geom(g)
+    a = dgamma(g)
+    m = np.arange(cg_.n_bins, dtype=np.float64)
+    t = np.zeros(cg_.n_bins)
+    t[0] = 1.0 / (8.0 * a * a)
+    odd = m % 2 == 1
+    t[odd] = -1.0 / (2.0 * np.pi ** 2 * np.sin(m[odd] * a) ** 2)
+    return t
+
+
+def fbp_filter(g, Y) -> np.ndarray:
+    """The filtering half of fan-beam FBP, per view:
+    Q(j) = alpha sum_k D cos(gamma_k) Y(k) g((j - k) alpha)."""
+    cg_ = _geom(g)
+    V, nb = cg_.n_views, cg_.n_bins
+    Y = _f64(Y).reshape(V, nb)
+    a = dgamma(g)
+    gam = (np.arange(nb) - 0.5 * (nb - 1)) * a
+    taps = fbp_taps(g)
+    full = np.concatenate([taps[:0:-1], taps])          # g(m), m = -(nb-1) .. nb-1
+    Q = np.empty((V, nb))
+    for v in range(V):
+        Q[v] = a * np.convolve(cg_.dso_mm * np.cos(gam) * Y[v], full)[nb - 1:2 * nb - 1]
+    return Q
+
+
+def fbp(g, Y, pixels=None) -> np.ndarray:
+    """Equiangular fan-beam filtered backprojection of a full 2 pi scan:
+      R'_v(j) = D cos(gamma_j) Y_v(j)                       (pre-weight)
+      Q_v(j)  = alpha sum_k R'_v(k) g((j - k) alpha)         (fan ramp, fbp_taps)
+      f(x, y) = dbeta sum_v Q_v(gamma'(x, y)) / L_v(x, y)^2  (weighted backprojection)
+    with D the source-isocentre distance, gamma' the fan angle of the pixel
+    centre seen from source v, L its distance from the source, dbeta = 2 pi/V,
+    and Q linearly interpolated between bins (zero beyond the detector).
+    ``pixels``: optional (iy, ix) index arrays; returns f at those pixels only."""
+    cg_ = _geom(g)
+    n, V, nb = cg_.n, cg_.n_views, cg_.n_bins
+    Qall = fbp_filter(g, Y)
+    a = dgamma(g)
+    D = cg_.dso_mm
+    jm = 0.5 * (nb - 1)
+    if pixels is None:
+        iy, ix = np.mgrid[0:n, 0:n]
+    else:
+        iy, ix = np.asarray(pixels[0]), np.asarray(pixels[1])
+    x = (ix + 0.5 - 0.5 * n) * cg_.pixel_mm
+    y = (iy + 0.5 - 0.5 * n) * cg_.pixel_mm
+    f = np.zeros(x.shape)
+    for v in range(V):
+        beta = cg_.beta0 + cg_.arc * v / V
+        Q = Qall[v]
+        Sx, Sy = D * np.cos(beta), D * np.sin(beta)
+        cx, cy = -np.cos(beta), -np.sin(beta)
+        ux, uy = x - Sx, y - Sy
+        gp = np.arctan2(cx * uy - cy * ux, cx * ux + cy * uy)
+        t = gp / a + jm
+        j0 = np.floor(t).astype(np.int64)
+        w = t - j0
+        Qz = np.concatenate([[0.0], Q, [0.0]])           # zero beyond the detector
+        q0 = Qz[np.clip(j0, -1, nb) + 1]
+        q1 = Qz[np.clip(j0 + 1, -1, nb) + 1]
+        f += ((1.0 - w) * q0 + w * q1) / (ux * ux + uy * uy)
+    return f * (cg_.arc / V)

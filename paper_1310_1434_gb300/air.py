@@ -31,7 +31,7 @@ EXPORTS = ["air_last_error", "air_plan_create", "air_plan_destroy", "air_plan_by
            "air_project",
            "air_filter", "air_backproject", "air_filtered_backproject", "air_filtered_backproject_noalloc",
            "air_framelet", "air_shrink",
-           "air_solve", "air_solve_l2", "air_solve_fbs", "air_solve_host", "air_solve_batch", "air_solve_batch_persistent", "air_server_create", "air_server_submit",
+           "air_solve", "air_solve_l2", "air_solve_fbs", "air_fbp", "air_solve_host", "air_solve_batch", "air_solve_batch_persistent", "air_server_create", "air_server_submit",
            "air_server_poll", "air_server_wait", "air_server_times", "air_server_destroy"]
 
 
@@ -87,6 +87,7 @@ def load(build_if_missing: bool = False):
         "air_solve": (i32, [P, P, f32, f32, i32, i32, P, P, P]),
         "air_solve_host": (i32, [P, P, f32, f32, i32, i32, P, P]),
         "air_solve_l2": (i32, [P, P, f32, i32, P, P]),
+        "air_fbp": (i32, [P, P, P, P]),
         "air_solve_fbs": (i32, [P, P, f32, f32, i32, P, P]),
         "air_solve_batch": (i32, [i32, P, P, P, P, P, P, P, P]),
         "air_solve_batch_persistent": (i32, [i32, P, P, P, P, P, P, P, P]),
@@ -256,6 +257,10 @@ def air_solve_l2(plan: Plan, Y, lam: float, n_cg: int, X, stream=None):
 def air_solve_fbs(plan: Plan, Y, lam: float, step: float, n_iter: int, X, stream=None):
     _check(load().air_solve_fbs(plan.handle, _ptr(Y), float(lam), float(step), int(n_iter), _ptr(X),
                                 _stream(stream)), "air_solve_fbs")
+
+
+def air_fbp(plan: Plan, Y, X, stream=None):
+    _check(load().air_fbp(plan.handle, _ptr(Y), _ptr(X), _stream(stream)), "air_fbp")
 
 
 def air_solve_host(plan: Plan, Y_host, lam: float, mu: float, n_outer: int, n_cg: int, X_host, stream=None):

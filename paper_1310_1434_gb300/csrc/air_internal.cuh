@@ -37,6 +37,7 @@ enum Op : int {
     OP_BWD_FIN,    // sum the backprojector's view parts, then the BwdMode epilogue
     OP_AXPY,       // q = x + step r            (forward step of Eq. 6, r = A'^T(Y - A x))
     OP_PROX,       // x = W^T S_tau(W q)        (framelet proximal step)
+    OP_FBP,        // ext_out = fan-beam FBP weighted backprojection of zc
     OP_COUNT
 };
 
@@ -104,6 +105,16 @@ struct SliceDesc {
     const unsigned *vt;  // [backprojector pixel tile][V] ray ranges (vt_pack)
     const float *taps;   // [nb] c0 * h[k], k = 0..nb-1 (h even)
     float ramp_diag;     // taps[0] + 2 sum_{odd m < nb} taps[m]
+    const float *prew;   // [nb] weights applied to the filter's input, or nullptr (FBP: cos gamma_j)
+    // fan-beam FBP (the analytic reconstruction): its filter runs the ramp
+    // tile with taps = fbp_taps, ramp_diag = fbp_diag, prew = fbp_w
+    const float2 *fview; // [V] central-ray direction of each view
+    const float *fbp_w;  // [nb] cos gamma_j
+    const float *fbp_taps;   // [nb] alpha D g(m alpha), the fan ramp
+    float fbp_diag;      // fbp_taps[0] + 2 sum_{odd m < nb} fbp_taps[m]
+    float dso_px;        // source-isocentre distance, pixels
+    float inv_dg, inv_dg_lo, jmid;   // 1 / fan pitch (high and low parts), (nb - 1) / 2
+    float fbp_scale;     // dbeta / dx^2
     // solver state (plan-owned workspace)
     float *x, *r, *p, *q, *rhs0, *g;   // n*n
     float *xp, *xt;                    // n*(n+2) each: zero-padded copy and transpose of the projector's input
@@ -159,7 +170,8 @@ __host__ __device__ inline int tiles_of(const SliceDesc &s, int op) {
     case OP_RAMP: return tiles_ramp(s);
     case OP_BWD: return tiles_bwd(s);
     case OP_CG_A: case OP_CG_B: case OP_ZERO: case OP_BWD_FIN: case OP_AXPY: return tiles_vec(s);
-    case OP_SHRINK: case OP_FRAMELET: case OP_FRAMELET_T: case OP_TRANSPOSE: case OP_PROX: return tiles_shr(s);
+    case OP_SHRINK: case OP_FRAMELET: case OP_FRAMELET_T: case OP_TRANSPOSE: case OP_PROX: case OP_FBP:
+        return tiles_shr(s);
     default: return 0;
     }
 }

@@ -102,6 +102,7 @@ size_t plan_bytes_estimate(const air_geometry &g) {
     size_t b = rays * sizeof(RayFx) + (size_t)g.n_views * tiles_bwd_xy(s) * 4 + (size_t)g.n_bins * 4;
     b += nn * 4 * (6 + 2 * parts + 18 + 1);      // x r p q rhs0 g, parts (up to 2x), b b2, xbuf
     b += (size_t)g.n * (g.n + 2) * 4 * 2;        // xp xt
+    b += (size_t)g.n_views * 8 + (size_t)g.n_bins * 8;   // FBP tables
     b += rays * 4 * 3;                           // z zc ybuf
     b += sizeof(CgState) + ((size_t)max_reduce_tiles(s) + 64) * 8 + 24 * 256;
     if (g.precision == AIR_PREC_BF16X3) {
@@ -301,6 +302,8 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     const size_t npad = (size_t)n * (n + 2);   // padded copies of the projector's input
     RayFx *ray;
     unsigned *vt;
+    float2 *fview;
+    float *fbw, *fbt;
     const int ntxy = tiles_bwd_xy(s);
     float *taps;
     CgState *cg;
@@ -309,7 +312,8 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     std::vector<Piece> pieces = {
         {(void **)&ray, rays * sizeof(RayFx)}, {(void **)&vt, (size_t)V * ntxy * sizeof(unsigned)},
         {(void **)&xp, npad * 4}, {(void **)&xt, npad * 4}, {(void **)&bpart, (size_t)parts_max * nn * 4},
-        {(void **)&taps, (size_t)nb * sizeof(float)},
+        {(void **)&taps, (size_t)nb * sizeof(float)}, {(void **)&fview, (size_t)V * sizeof(float2)},
+        {(void **)&fbw, (size_t)nb * sizeof(float)}, {(void **)&fbt, (size_t)nb * sizeof(float)},
         {(void **)&x, nn * 4}, {(void **)&r, nn * 4}, {(void **)&p, nn * 4}, {(void **)&q, nn * 4},
         {(void **)&rhs0, nn * 4}, {(void **)&gg, nn * 4}, {(void **)&b, 9 * nn * 4}, {(void **)&b2, 9 * nn * 4},
         {(void **)&z, rays * 4}, {(void **)&zc, rays * 4}, {(void **)&ybuf, rays * 4}, {(void **)&xbuf, nn * 4},
@@ -415,9 +419,36 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
         diag += k == 0 ? h : 2.0 * h;
     }
     s.ramp_diag = (float)(c0 * diag);
+    // fan-beam FBP (full scans): per view the central direction; per bin the
+    // pre-weight cos gamma_j and the fan ramp alpha D g(m alpha), g(0) =
+    // 1/(8 alpha^2), g(odd m) = -1/(2 pi^2 sin^2(m alpha)), g(even m) = 0
+    std::vector<float2> hfview(V);
+    std::vector<float> hfbw(nb), hfbt(nb);
+    for (int v = 0; v < V; ++v) {
+        const double beta = g.beta0 + g.arc * (double)v / (double)V;
+        hfview[v] = make_float2((float)(-std::cos(beta)), (float)(-std::sin(beta)));
+    }
+    double fdiag = 0.0;
+    for (int k = nb - 1; k >= 0; --k) {
+        const double gm = k == 0 ? 1.0 / (8.0 * dg * dg)
+                                 : (k % 2 ? -1.0 / (2.0 * M_PI * M_PI * std::sin(k * dg) * std::sin(k * dg)) : 0.0);
+        const double t = dg * g.dso_mm * gm;
+        hfbt[k] = (float)t;
+        fdiag += k == 0 ? t : 2.0 * t;
+        hfbw[k] = (float)std::cos(((double)k - 0.5 * (nb - 1)) * dg);
+    }
+    s.fbp_diag = (float)fdiag;
+    s.dso_px = (float)(g.dso_mm / g.pixel_mm);
+    s.inv_dg = (float)(1.0 / dg);
+    s.inv_dg_lo = (float)(1.0 / dg - (double)s.inv_dg);
+    s.jmid = 0.5f * (nb - 1);
+    s.fbp_scale = (float)(g.arc / (double)V / (g.pixel_mm * g.pixel_mm));
     cudaError_t e = cudaMemcpy(ray, hray.data(), rays * sizeof(RayFx), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(vt, hvt.data(), hvt.size() * sizeof(unsigned), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(taps, htaps.data(), nb * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(fview, hfview.data(), V * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(fbw, hfbw.data(), nb * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(fbt, hfbt.data(), nb * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(cg, 0, sizeof(CgState));
     if (e == cudaSuccess) e = cudaMemset(xp, 0, npad * 4);   // the pads stay zero
     if (e == cudaSuccess) e = cudaMemset(xt, 0, npad * 4);
@@ -427,6 +458,9 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     }
     s.ray = ray;
     s.vt = vt;
+    s.fview = fview;
+    s.fbp_w = fbw;
+    s.fbp_taps = fbt;
     s.taps = taps;
     s.x = x; s.r = r; s.p = p; s.q = q; s.rhs0 = rhs0; s.g = gg; s.b = b; s.b2 = b2; s.xp = xp; s.xt = xt;
     s.bwd_part = bpart;
@@ -766,6 +800,28 @@ extern "C" air_status air_solve_fbs(const air_plan *P, const float *Y, float lam
     s.tau = step * lambda;      // the proximal threshold
     s.step = step;
     return run_program_single(P, s, fbs_program(n_iter, tc), (cudaStream_t)stream);
+}
+
+extern "C" air_status air_fbp(const air_plan *P, const float *Y, float *X, air_stream stream) {
+    if (!P) return fail(AIR_ERR_INVALID_ARG, "plan is NULL");
+    if (std::fabs(P->geom.arc - 2.0 * M_PI) > 1e-9 * 2.0 * M_PI)
+        return fail(AIR_ERR_INVALID_ARG, "FBP needs a full 2 pi scan");
+    TRY(check_dev_ptr(Y, "Y"));
+    TRY(check_dev_ptr(X, "X"));
+    if (overlap(X, img_bytes(P), Y, sino_bytes(P))) return fail(AIR_ERR_INVALID_ARG, "X and Y overlap");
+    const cudaStream_t st = (cudaStream_t)stream;
+    SliceDesc f = P->desc;        // the filter: the ramp tile with the fan ramp and pre-weight
+    f.filter = AIR_FILTER_RAMLAK;
+    f.taps = f.fbp_taps;
+    f.ramp_diag = f.fbp_diag;
+    f.prew = f.fbp_w;
+    f.ext_in = Y;
+    f.ext_out = P->desc.zc;
+    CUDA_TRY(launch_op(OP_RAMP, f, RSRC_EXT, st));
+    SliceDesc b = P->desc;
+    b.ext_out = X;
+    CUDA_TRY(launch_op(OP_FBP, b, 0, st));
+    return AIR_OK;
 }
 
 extern "C" air_status air_solve_host(const air_plan *P, const float *Y_host, float lambda, float mu,

@@ -30,6 +30,8 @@ __global__ void __launch_bounds__(AIR_THREADS) k_op(const SliceDesc s, int arg) 
         tile_axpy(s, tile);
     } else if constexpr (OP == OP_PROX) {
         tile_prox(s, tile, sm);
+    } else if constexpr (OP == OP_FBP) {
+        tile_fbp(s, tile);
     } else if constexpr (OP == OP_SHRINK) {
         if (arg < 2) {
             ShrinkArgs a{s.x, arg ? s.b2 : s.b, arg ? s.b : s.b2, s.g, s.tau};
@@ -76,6 +78,7 @@ cudaError_t launch_op(int op, const SliceDesc &s, int arg, cudaStream_t st) {
     case OP_BWD_FIN: return launch_one<OP_BWD_FIN>(s, arg, st);
     case OP_AXPY: return launch_one<OP_AXPY>(s, arg, st);
     case OP_PROX: return launch_one<OP_PROX>(s, arg, st);
+    case OP_FBP: return launch_one<OP_FBP>(s, arg, st);
     default: return cudaErrorInvalidValue;
     }
 }

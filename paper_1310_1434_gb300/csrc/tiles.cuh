@@ -333,9 +333,10 @@ __device__ __forceinline__ void tile_ramp(const SliceDesc &s, int arg, int tile,
     const int PO = nb + 2;
     const int plen = 3 * nb + 2 * RAMP_R + 4;
     float *P = sm, *tp = sm + plen;
+    const float *__restrict__ pw = s.prew;
     for (int k = threadIdx.x; k < plen; k += AIR_THREADS) {
         const int i = k - PO;
-        P[k] = (i >= 0 && i < nb) ? src[off + i] : 0.f;
+        P[k] = (i >= 0 && i < nb) ? (pw ? src[off + i] * __ldg(pw + i) : src[off + i]) : 0.f;
     }
     for (int k = threadIdx.x; k < nb; k += AIR_THREADS) tp[k] = __ldg(s.taps + k);
     __syncthreads();
@@ -372,6 +373,65 @@ __device__ __forceinline__ void tile_ramp(const SliceDesc &s, int arg, int tile,
             if (j0 + i < nb) dst[off + j0 + i] = fmaf(diag, ctr[i], acc[i]);
     }
     __syncthreads();
+}
+
+// ======================================================================
+// Fan-beam FBP (the analytic reconstruction the Materials section compares
+// AIR with; the textbook equiangular algorithm): after the filter
+// Q_v(j) = sum_k fbp_taps[|j-k|] cos(gamma_k) Y_v(k), the weighted
+// backprojection
+//   f(x, y) = dbeta / dx^2 sum_v Q_v(gamma') / L^2
+// with gamma' the fan angle of the pixel centre seen from the source of view
+// v, L its distance from the source (pixels), and Q linearly interpolated
+// between bins, zero beyond the detector.  With the central direction
+// c = (cx, cy) of the view (the central ray passes through the centre), the
+// source-relative products are L sin(gamma') = cx y - cy x and
+// L cos(gamma') = D + cx x + cy y, which stay accurate in FP32.
+// One thread per pixel, 16 x 16 pixels per block.
+// ======================================================================
+// arctan(u) for |u| <= 0.45 by its Maclaurin (Gregory) series through u^13;
+// the alternating-series remainder is below 0.45^15/15 = 4.2e-7 rad.
+__device__ __forceinline__ float atan_series(float u) {
+    const float w = u * u;
+    float p = 1.f / 13.f;
+    p = fmaf(p, w, -1.f / 11.f);
+    p = fmaf(p, w, 1.f / 9.f);
+    p = fmaf(p, w, -1.f / 7.f);
+    p = fmaf(p, w, 1.f / 5.f);
+    p = fmaf(p, w, -1.f / 3.f);
+    p = fmaf(p, w, 1.f);
+    return u * p;
+}
+
+__device__ __forceinline__ void tile_fbp(const SliceDesc &s, int tile) {
+    const int n = s.n, nb = s.nb, tpr = (n + SHR_T - 1) / SHR_T;
+    const int ix = (tile % tpr) * SHR_T + (int)threadIdx.x % SHR_T;
+    const int iy = (tile / tpr) * SHR_T + (int)threadIdx.x / SHR_T;
+    if (ix >= n || iy >= n) return;
+    const float x = (float)ix + 0.5f - s.half_n, y = (float)iy + 0.5f - s.half_n;
+    const float *__restrict__ Q = s.zc;
+    float acc = 0.f;
+#pragma unroll 2
+    for (int v = 0; v < s.V; ++v, Q += nb) {
+        const float2 c = __ldg(s.fview + v);
+        const float cr = fmaf(c.x, y, -c.y * x);                 // L sin(gamma')
+        const float dt = fmaf(c.x, x, fmaf(c.y, y, s.dso_px));   // L cos(gamma') > 0
+        const float u = cr / dt;
+        const float gp = fabsf(u) <= 0.45f ? atan_series(u) : atan2f(cr, dt);
+        // bin position t = gp / alpha + jmid: its integer part from a rounded
+        // t, its fraction as an FMA residual against that integer with 1/alpha
+        // in two parts, so neither t's magnitude (~n_b/2) nor 1/alpha's
+        // rounding costs digits of the interpolation weight
+        const float tr = floorf(fmaf(gp, s.inv_dg, s.jmid));
+        float w = fmaf(gp, s.inv_dg, s.jmid - tr);
+        w = fmaf(gp, s.inv_dg_lo, w);
+        const int j0 = (int)tr + (w < 0.f ? -1 : (w >= 1.f ? 1 : 0));
+        w = w < 0.f ? w + 1.f : (w >= 1.f ? w - 1.f : w);
+        const float q0 = (unsigned)j0 < (unsigned)nb ? __ldg(Q + j0) : 0.f;
+        const float q1 = (unsigned)(j0 + 1) < (unsigned)nb ? __ldg(Q + j0 + 1) : 0.f;
+        acc += __fdividef(fmaf(w, q1 - q0, q0), fmaf(cr, cr, dt * dt));
+    }
+    s.ext_out[(size_t)iy * n + ix] = s.fbp_scale * acc;
 }
 
 // ======================================================================
@@ -715,6 +775,7 @@ __device__ __forceinline__ void run_tile(const SliceDesc &s, int op, int arg, in
     case OP_ZERO: tile_zero(s, tile); break;
     case OP_AXPY: tile_axpy(s, tile); break;
     case OP_PROX: tile_prox(s, tile, sm); break;
+    case OP_FBP: tile_fbp(s, tile); break;
     case OP_SHRINK: {   // arg = parity of the outer step: b -> b2, then b2 -> b
         ShrinkArgs a{s.x, arg ? s.b2 : s.b, arg ? s.b : s.b2, s.g, s.tau};
         tile_shrink(s, a, tile, true, nullptr, sm);
