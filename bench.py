@@ -52,6 +52,8 @@ def parse():
                     choices=["fwd", "bwd", "ramp", "ramp_tc", "shrink", "solve", "plain", "batch"],
                     help="profiling mode: run one operator on the 512^2/800-view slice --reps times")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--batch64", type=int, default=1,
+                    help="also time the 64-slice batch of uneven geometry (0 skips it)")
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests in each bounded serving trace (0 skips the serving measurement)")
     return ap.parse_args()
@@ -440,6 +442,27 @@ def main():
             lambda: air.air_solve_batch_persistent(plans32, Yd, lam, mu, no, ncg, Xd)),
     }
 
+    # ---- the 64-slice batch of uneven geometry (256^2/200 views, 512^2/400,
+    # 512^2/800, 768^2/800 bins 384/738/738/1024; seeds 100..163), FP32 ----
+    config64 = None
+    if args.batch64:
+        w64 = inputs.batch_workloads(64, first_seed=100 + 1000 * rank)
+        Y64 = [torch.as_tensor(inputs.make_case(w)[2].astype(np.float32).ravel(), device=dev) for w in w64]
+        t0 = time.perf_counter()
+        p64 = [air.Plan(w.geom) for w in w64]
+        t_plans = time.perf_counter() - t0
+        X64 = [torch.empty(w.geom.n ** 2, device=dev) for w in w64]
+        args64 = ([w.lam for w in w64], [w.mu for w in w64], [w.n_outer for w in w64], [w.n_cg for w in w64])
+        config64 = {"slices": 64, "shapes": "16 each of 256^2/200, 512^2/400, 512^2/800, 768^2/800",
+                    "plan_create_s": t_plans}
+        for form, fn in (("grouped_graph", air.air_solve_batch), ("persistent", air.air_solve_batch_persistent)):
+            fn(p64, Y64, *args64[:2], *args64[2:], X64)          # first call builds and captures the graph
+            flush.zero_()
+            t = events_time(torch, stream, lambda: fn(p64, Y64, *args64[:2], *args64[2:], X64), 1)
+            config64[f"{form}_slices_per_s"] = 64 * 1000.0 / t
+            config64[f"{form}_ms"] = t
+        del p64, X64, Y64
+
     # ---- serving: continuous batching of a bounded Poisson trace ----
     serving = None
     if args.serve_requests > 0:
@@ -564,6 +587,7 @@ def main():
                       "ms_800_views": float(np.mean(lat[800])) if lat[800] else None,
                       "ms_200_views": float(np.mean(lat[200])) if lat[200] else None},
         "serving": serving,
+        "batch64_uneven": config64,
         "next_rows": next_rows,
         "latency_batch": {"p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
                           "note": "every slice of a batch completes with the batch"},

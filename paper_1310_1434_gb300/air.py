@@ -298,29 +298,41 @@ class Server:
         _check(load().air_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h)),
                "air_server_create")
         self.handle = h.value
+        self._side = {}    # request id -> image side, so result buffers are always n*n
 
     def submit(self, geom, Y_host, lam: float, mu: float, n_outer: int, n_cg: int) -> int:
         import numpy as np
-        g = Geometry.of(geom).c()
+        gg = Geometry.of(geom)
+        g = gg.c()
         Y = np.ascontiguousarray(Y_host, dtype=np.float32)
+        if Y.size != gg.n_views * gg.n_bins:
+            raise ValueError(f"Y has {Y.size} values, the geometry {gg.n_views * gg.n_bins}")
         rid = ctypes.c_uint64()
         _check(load().air_server_submit(self.handle, ctypes.byref(g), Y.ctypes.data, float(lam), float(mu),
                                         int(n_outer), int(n_cg), ctypes.byref(rid)), "air_server_submit")
+        self._side[rid.value] = gg.n
         return rid.value
 
-    def poll(self, rid: int, n: int):
-        """The image (n*n float32) once finished, else None."""
+    def _image(self, rid: int, n):
         import numpy as np
-        X = np.empty(n * n, np.float32)
+        side = self._side.get(rid)
+        if side is None:
+            raise KeyError(f"request {rid} was not submitted through this Server")
+        if n is not None and int(n) != side:
+            raise ValueError(f"request {rid} has a {side} x {side} image, not {n} x {n}")
+        return np.empty(side * side, np.float32)
+
+    def poll(self, rid: int, n: int = None):
+        """The image (n*n float32) once finished, else None."""
+        X = self._image(rid, n)
         st = load().air_server_poll(self.handle, rid, X.ctypes.data)
         if st == AIR_ERR_NOT_READY:
             return None
         _check(st, "air_server_poll")
         return X
 
-    def wait(self, rid: int, n: int):
-        import numpy as np
-        X = np.empty(n * n, np.float32)
+    def wait(self, rid: int, n: int = None):
+        X = self._image(rid, n)
         _check(load().air_server_wait(self.handle, rid, X.ctypes.data), "air_server_wait")
         return X
 

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -279,6 +280,172 @@ air_status autotune(air_plan *P) {
 }
 }  // namespace air
 
+// ------------------------------------------------------------ geometry tables
+// The host-side tables of a geometry (FP64 arithmetic, stored as the device
+// formats), cached per geometry for the process: plans of one geometry (a
+// batch, the server's pool) share one computation.
+namespace {
+struct HostTables {
+    std::vector<RayFx> ray;
+    std::vector<unsigned> vt;
+    std::vector<float> taps, fbw, fbt;
+    std::vector<float2> fview;
+    float ramp_diag = 0.f, fbp_diag = 0.f;
+};
+
+air_status build_tables(const air_geometry &g, double dg, int ntxy, HostTables &T) {
+    const int n = g.n, V = g.n_views, nb = g.n_bins;
+    const size_t rays = (size_t)V * nb;
+    // geometry tables, computed in FP64: per view the source (pixel units,
+    // centred) and the central-ray direction; per ray the fixed-point line
+    std::vector<RayFx> &hray = T.ray;
+    hray.resize(rays);
+    std::vector<double4> hsrc(V);   // per view: source (pixel units, centred), central direction
+    std::vector<float> &htaps = T.taps;
+    htaps.resize(nb);
+    const double inv_dx = 1.0 / g.pixel_mm;
+    for (int v = 0; v < V; ++v) {
+        const double beta = g.beta0 + g.arc * (double)v / (double)V;
+        const double cb = std::cos(beta), sb = std::sin(beta);
+        const double Sx = g.dso_mm * cb, Sy = g.dso_mm * sb;
+        hsrc[v] = make_double4(Sx * inv_dx, Sy * inv_dx, -cb, -sb);
+        for (int j = 0; j < nb; ++j) {
+            const double gamma = ((double)j - 0.5 * (nb - 1)) * dg;
+            const double th = beta + M_PI + gamma;
+            const double ux = std::cos(th), uy = std::sin(th);
+            const double su = Sx * ux + Sy * uy;
+            // closest point to the image centre, pixel units, origin at the image corner
+            const double px = (Sx - su * ux) * inv_dx + 0.5 * n, py = (Sy - su * uy) * inv_dx + 0.5 * n;
+            hray[(size_t)v * nb + j] = make_ray_fx(px, py, ux, uy, n);
+        }
+    }
+    // the projector walks [k0, k1) without bounds checks (the image copies
+    // it reads are padded by one entry per row end): every walked column must
+    // lie in the image and its span start in rows [-1, n-1]
+    for (const RayFx &r : hray) {
+        const int k0 = r.kk & 0xffff, k1 = r.kk >> 16;
+        bool ok = 0 <= k0 && k0 <= k1 && k1 <= n;
+        for (int k : {k0, k1 - 1}) {
+            if (!ok || k0 == k1) break;
+            const long long r0 = (r.L0 + (long long)k * ray_M(r)) >> 32;
+            ok = r0 >= -1 && r0 <= n - 1;
+        }
+        if (!ok) return fail(AIR_ERR_INTERNAL, "ray table: a walk range leaves the image");
+    }
+    // backprojector ray ranges: per view and 16 x 16 pixel tile, the rays
+    // whose fan angle lies between the extreme fan angles of the tile's
+    // corners (the tile is convex and the source outside it, so exactly
+    // these rays can meet it), widened by 0.02 bin; and whether they all walk
+    // the same way.  Fan angles at the corner grid are shared by neighbouring
+    // tiles.
+    const int tpr = (n + BWD_T - 1) / BWD_T;
+    std::vector<unsigned> &hvt = T.vt;
+    hvt.assign((size_t)V * ntxy, 0u);
+    {
+        std::vector<double> gam((size_t)(tpr + 1) * (tpr + 1));
+        std::vector<int> chg(nb);   // number of orientation changes among rays 0..j
+        const double jm = 0.5 * (nb - 1);
+        for (int v = 0; v < V; ++v) {
+            const double4 w = hsrc[v];
+            for (int iy = 0; iy <= tpr; ++iy)
+                for (int ix = 0; ix <= tpr; ++ix) {
+                    const double px = std::min(ix * BWD_T, n) - 0.5 * n, py = std::min(iy * BWD_T, n) - 0.5 * n;
+                    const double dxs = px - w.x, dys = py - w.y;
+                    gam[(size_t)iy * (tpr + 1) + ix] = std::atan2(w.z * dys - w.w * dxs, w.z * dxs + w.w * dys);
+                }
+            const RayFx *rv = hray.data() + (size_t)v * nb;
+            chg[0] = 0;
+            for (int j = 1; j < nb; ++j) chg[j] = chg[j - 1] + (rv[j].o != rv[j - 1].o);
+            for (int ty = 0; ty < tpr; ++ty)
+                for (int tx = 0; tx < tpr; ++tx) {
+                    double gmin = 1e30, gmax = -1e30;
+                    for (int cy = 0; cy < 2; ++cy)
+                        for (int cx = 0; cx < 2; ++cx) {
+                            const double gc = gam[(size_t)(ty + cy) * (tpr + 1) + tx + cx];
+                            gmin = std::min(gmin, gc);
+                            gmax = std::max(gmax, gc);
+                        }
+                    const double f0 = std::ceil(gmin / dg + jm - 0.02), f1 = std::floor(gmax / dg + jm + 0.02);
+                    const int j0 = (int)std::max(0.0, std::min(f0, (double)nb));
+                    const int j1 = (int)std::max(-1.0, std::min(f1, (double)nb - 1));   // inclusive
+                    unsigned ent = vt_pack(0, 0, 0, false);
+                    if (j1 >= j0) ent = vt_pack(j0, j1 + 1, rv[j0].o, chg[j1] != chg[j0]);
+                    hvt[(size_t)(ty * tpr + tx) * V + v] = ent;
+                }
+        }
+    }
+    const double c0 = M_PI / ((double)V * g.pixel_mm * g.pixel_mm);
+    double diag = 0.0;   // h[0] + 2 sum_{odd m < nb} h[m]: the difference form's centre weight
+    for (int k = nb - 1; k >= 0; --k) {
+        const double h = k == 0 ? 0.25 : (k % 2 ? -1.0 / (M_PI * M_PI * (double)k * (double)k) : 0.0);
+        htaps[k] = (float)(c0 * h);
+        diag += k == 0 ? h : 2.0 * h;
+    }
+    T.ramp_diag = (float)(c0 * diag);
+    // fan-beam FBP (full scans): per view the central direction; per bin the
+    // pre-weight cos gamma_j and the fan ramp alpha D g(m alpha), g(0) =
+    // 1/(8 alpha^2), g(odd m) = -1/(2 pi^2 sin^2(m alpha)), g(even m) = 0
+    std::vector<float2> &hfview = T.fview;
+    std::vector<float> &hfbw = T.fbw, &hfbt = T.fbt;
+    hfview.resize(V);
+    hfbw.resize(nb);
+    hfbt.resize(nb);
+    for (int v = 0; v < V; ++v) {
+        const double beta = g.beta0 + g.arc * (double)v / (double)V;
+        hfview[v] = make_float2((float)(-std::cos(beta)), (float)(-std::sin(beta)));
+    }
+    double fdiag = 0.0;
+    for (int k = nb - 1; k >= 0; --k) {
+        const double gm = k == 0 ? 1.0 / (8.0 * dg * dg)
+                                 : (k % 2 ? -1.0 / (2.0 * M_PI * M_PI * std::sin(k * dg) * std::sin(k * dg)) : 0.0);
+        const double t = dg * g.dso_mm * gm;
+        hfbt[k] = (float)t;
+        fdiag += k == 0 ? t : 2.0 * t;
+        hfbw[k] = (float)std::cos(((double)k - 0.5 * (nb - 1)) * dg);
+    }
+    T.fbp_diag = (float)fdiag;
+    return AIR_OK;
+}
+
+struct GeomKey {
+    int n, V, nb;
+    double dx, dso, dg, beta0, arc;
+    bool operator<(const GeomKey &o) const { return std::memcmp(this, &o, sizeof(GeomKey)) < 0; }
+};
+std::mutex g_tables_mu;
+std::map<GeomKey, std::shared_ptr<const HostTables>> g_tables;
+constexpr size_t TABLE_CACHE_MAX = 16;
+
+air_status geometry_tables(const air_geometry &g, double dg, int ntxy, std::shared_ptr<const HostTables> *out) {
+    GeomKey key;
+    std::memset(&key, 0, sizeof(key));
+    key.n = g.n;
+    key.V = g.n_views;
+    key.nb = g.n_bins;
+    key.dx = g.pixel_mm;
+    key.dso = g.dso_mm;
+    key.dg = dg;
+    key.beta0 = g.beta0;
+    key.arc = g.arc;
+    {
+        std::lock_guard<std::mutex> lock(g_tables_mu);
+        auto it = g_tables.find(key);
+        if (it != g_tables.end()) {
+            *out = it->second;
+            return AIR_OK;
+        }
+    }
+    auto T = std::make_shared<HostTables>();
+    air_status st = build_tables(g, dg, ntxy, *T);
+    if (st != AIR_OK) return st;
+    std::lock_guard<std::mutex> lock(g_tables_mu);
+    if (g_tables.size() >= TABLE_CACHE_MAX) g_tables.erase(g_tables.begin());
+    g_tables[key] = T;
+    *out = T;
+    return AIR_OK;
+}
+}  // namespace
+
 air_status plan_build(const air_geometry *geom, air_plan *P) {
     const air_geometry &g = *geom;
     const int n = g.n, V = g.n_views, nb = g.n_bins;
@@ -333,111 +500,17 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
         off += pc.bytes;
     }
 
-    // geometry tables, computed in FP64: per view the source (pixel units,
-    // centred) and the central-ray direction; per ray the fixed-point line
-    std::vector<RayFx> hray(rays);
-    std::vector<double4> hsrc(V);   // per view: source (pixel units, centred), central direction
-    std::vector<float> htaps(nb);
-    const double inv_dx = 1.0 / g.pixel_mm;
-    for (int v = 0; v < V; ++v) {
-        const double beta = g.beta0 + g.arc * (double)v / (double)V;
-        const double cb = std::cos(beta), sb = std::sin(beta);
-        const double Sx = g.dso_mm * cb, Sy = g.dso_mm * sb;
-        hsrc[v] = make_double4(Sx * inv_dx, Sy * inv_dx, -cb, -sb);
-        for (int j = 0; j < nb; ++j) {
-            const double gamma = ((double)j - 0.5 * (nb - 1)) * dg;
-            const double th = beta + M_PI + gamma;
-            const double ux = std::cos(th), uy = std::sin(th);
-            const double su = Sx * ux + Sy * uy;
-            // closest point to the image centre, pixel units, origin at the image corner
-            const double px = (Sx - su * ux) * inv_dx + 0.5 * n, py = (Sy - su * uy) * inv_dx + 0.5 * n;
-            hray[(size_t)v * nb + j] = make_ray_fx(px, py, ux, uy, n);
-        }
+    std::shared_ptr<const HostTables> T;
+    if (air_status st = geometry_tables(g, dg, ntxy, &T); st != AIR_OK) {
+        cudaFree(mem);
+        return st;
     }
-    // the projector walks [k0, k1) without bounds checks (the image copies
-    // it reads are padded by one entry per row end): every walked column must
-    // lie in the image and its span start in rows [-1, n-1]
-    for (const RayFx &r : hray) {
-        const int k0 = r.kk & 0xffff, k1 = r.kk >> 16;
-        bool ok = 0 <= k0 && k0 <= k1 && k1 <= n;
-        for (int k : {k0, k1 - 1}) {
-            if (!ok || k0 == k1) break;
-            const long long r0 = (r.L0 + (long long)k * ray_M(r)) >> 32;
-            ok = r0 >= -1 && r0 <= n - 1;
-        }
-        if (!ok) {
-            cudaFree(mem);
-            return fail(AIR_ERR_INTERNAL, "ray table: a walk range leaves the image");
-        }
-    }
-    // backprojector ray ranges: per view and 16 x 16 pixel tile, the rays
-    // whose fan angle lies between the extreme fan angles of the tile's
-    // corners (the tile is convex and the source outside it, so exactly
-    // these rays can meet it), widened by 0.02 bin; and whether they all walk
-    // the same way.  Fan angles at the corner grid are shared by neighbouring
-    // tiles.
-    const int tpr = (n + BWD_T - 1) / BWD_T;
-    std::vector<unsigned> hvt((size_t)V * ntxy);
-    {
-        std::vector<double> gam((size_t)(tpr + 1) * (tpr + 1));
-        std::vector<int> chg(nb);   // number of orientation changes among rays 0..j
-        const double jm = 0.5 * (nb - 1);
-        for (int v = 0; v < V; ++v) {
-            const double4 w = hsrc[v];
-            for (int iy = 0; iy <= tpr; ++iy)
-                for (int ix = 0; ix <= tpr; ++ix) {
-                    const double px = std::min(ix * BWD_T, n) - 0.5 * n, py = std::min(iy * BWD_T, n) - 0.5 * n;
-                    const double dxs = px - w.x, dys = py - w.y;
-                    gam[(size_t)iy * (tpr + 1) + ix] = std::atan2(w.z * dys - w.w * dxs, w.z * dxs + w.w * dys);
-                }
-            const RayFx *rv = hray.data() + (size_t)v * nb;
-            chg[0] = 0;
-            for (int j = 1; j < nb; ++j) chg[j] = chg[j - 1] + (rv[j].o != rv[j - 1].o);
-            for (int ty = 0; ty < tpr; ++ty)
-                for (int tx = 0; tx < tpr; ++tx) {
-                    double gmin = 1e30, gmax = -1e30;
-                    for (int cy = 0; cy < 2; ++cy)
-                        for (int cx = 0; cx < 2; ++cx) {
-                            const double gc = gam[(size_t)(ty + cy) * (tpr + 1) + tx + cx];
-                            gmin = std::min(gmin, gc);
-                            gmax = std::max(gmax, gc);
-                        }
-                    const double f0 = std::ceil(gmin / dg + jm - 0.02), f1 = std::floor(gmax / dg + jm + 0.02);
-                    const int j0 = (int)std::max(0.0, std::min(f0, (double)nb));
-                    const int j1 = (int)std::max(-1.0, std::min(f1, (double)nb - 1));   // inclusive
-                    unsigned ent = vt_pack(0, 0, 0, false);
-                    if (j1 >= j0) ent = vt_pack(j0, j1 + 1, rv[j0].o, chg[j1] != chg[j0]);
-                    hvt[(size_t)(ty * tpr + tx) * V + v] = ent;
-                }
-        }
-    }
-    const double c0 = M_PI / ((double)V * g.pixel_mm * g.pixel_mm);
-    double diag = 0.0;   // h[0] + 2 sum_{odd m < nb} h[m]: the difference form's centre weight
-    for (int k = nb - 1; k >= 0; --k) {
-        const double h = k == 0 ? 0.25 : (k % 2 ? -1.0 / (M_PI * M_PI * (double)k * (double)k) : 0.0);
-        htaps[k] = (float)(c0 * h);
-        diag += k == 0 ? h : 2.0 * h;
-    }
-    s.ramp_diag = (float)(c0 * diag);
-    // fan-beam FBP (full scans): per view the central direction; per bin the
-    // pre-weight cos gamma_j and the fan ramp alpha D g(m alpha), g(0) =
-    // 1/(8 alpha^2), g(odd m) = -1/(2 pi^2 sin^2(m alpha)), g(even m) = 0
-    std::vector<float2> hfview(V);
-    std::vector<float> hfbw(nb), hfbt(nb);
-    for (int v = 0; v < V; ++v) {
-        const double beta = g.beta0 + g.arc * (double)v / (double)V;
-        hfview[v] = make_float2((float)(-std::cos(beta)), (float)(-std::sin(beta)));
-    }
-    double fdiag = 0.0;
-    for (int k = nb - 1; k >= 0; --k) {
-        const double gm = k == 0 ? 1.0 / (8.0 * dg * dg)
-                                 : (k % 2 ? -1.0 / (2.0 * M_PI * M_PI * std::sin(k * dg) * std::sin(k * dg)) : 0.0);
-        const double t = dg * g.dso_mm * gm;
-        hfbt[k] = (float)t;
-        fdiag += k == 0 ? t : 2.0 * t;
-        hfbw[k] = (float)std::cos(((double)k - 0.5 * (nb - 1)) * dg);
-    }
-    s.fbp_diag = (float)fdiag;
+    const std::vector<RayFx> &hray = T->ray;
+    const std::vector<unsigned> &hvt = T->vt;
+    const std::vector<float> &htaps = T->taps, &hfbw = T->fbw, &hfbt = T->fbt;
+    const std::vector<float2> &hfview = T->fview;
+    s.ramp_diag = T->ramp_diag;
+    s.fbp_diag = T->fbp_diag;
     s.dso_px = (float)(g.dso_mm / g.pixel_mm);
     s.inv_dg = (float)(1.0 / dg);
     s.inv_dg_lo = (float)(1.0 / dg - (double)s.inv_dg);

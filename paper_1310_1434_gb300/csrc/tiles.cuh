@@ -23,7 +23,25 @@ namespace air {
 // ======================================================================
 __host__ __device__ inline int pad_ld(int n) { return n + 2; }   // row stride of the padded copies
 
-// sum over the walk of ov * X (without c), from the padded copies
+// One column of the walk: the overlaps of the span [lo, lo + Ma] with row r0
+// and (when lo32 + Ma wraps past 2^32) row r0 + 1, times the pixel values.
+__device__ __forceinline__ void fx_step(long long &lo, const float *__restrict__ &row, long long M, unsigned Ma,
+                                        int ld, float &a0, float &a1) {
+    const int r0 = (int)(lo >> 32);
+    const unsigned t = (unsigned)lo + Ma;
+    const unsigned ov1 = t < Ma ? t : 0u;      // t < Ma iff the add wrapped
+    const unsigned ov0 = Ma - ov1;
+    a0 = fmaf(__uint2float_rn(ov0), __ldg(row + r0), a0);
+    if (ov1 != 0u) a1 = fmaf(__uint2float_rn(ov1), __ldg(row + r0 + 1), a1);
+    lo += M;
+    row += ld;
+}
+
+// Sum over the walk of ov * X (without c), from the padded copies.
+// Consecutive columns alternate between two accumulator pairs: four FP32
+// accumulators of about a quarter of the terms each (two independent FMA
+// chains), which keeps the ray sum's rounding error within the
+// single-application bound for images up to 1024^2.
 __device__ __forceinline__ float fx_ray(const float *__restrict__ XP, const float *__restrict__ XTP, int n,
                                         const RayFx &r) {
     const int k0 = r.kk & 0xffff, k1 = r.kk >> 16;
@@ -32,19 +50,14 @@ __device__ __forceinline__ float fx_ray(const float *__restrict__ XP, const floa
     const long long M = ray_M(r);
     const unsigned Ma = r.Ma;
     long long lo = r.L0 + (long long)k0 * M;
-    float a0 = 0.f, a1 = 0.f;
-#pragma unroll 2
-    for (int k = k0; k < k1; ++k) {
-        const int r0 = (int)(lo >> 32);
-        const unsigned t = (unsigned)lo + Ma;
-        const unsigned ov1 = t < Ma ? t : 0u;      // t < Ma iff the add wrapped
-        const unsigned ov0 = Ma - ov1;
-        a0 = fmaf(__uint2float_rn(ov0), __ldg(row + r0), a0);
-        if (ov1 != 0u) a1 = fmaf(__uint2float_rn(ov1), __ldg(row + r0 + 1), a1);
-        lo += M;
-        row += ld;
+    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+    int k = k0;
+    for (; k + 1 < k1; k += 2) {
+        fx_step(lo, row, M, Ma, ld, a0, a1);
+        fx_step(lo, row, M, Ma, ld, b0, b1);
     }
-    return a0 + a1;
+    if (k < k1) fx_step(lo, row, M, Ma, ld, a0, a1);
+    return (a0 + a1) + (b0 + b1);
 }
 
 __device__ __forceinline__ void tile_fwd(const SliceDesc &s, int arg, int tile) {

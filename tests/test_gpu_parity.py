@@ -253,9 +253,11 @@ def test_invalid_arguments_are_rejected():
 
 # --------------------------------------------------------- full size ----
 BIG = [inputs.AIR512_V200, inputs.AIR512_V800]
+# single applications also at the largest shape of the 64-slice batch
+BIG_OPS = BIG + [inputs._wl("batch768_v800", 768, 0.8 * 512 / 768, 800, 1024, 103, 8, 4, 2e4)]
 
 
-@pytest.mark.parametrize("w", BIG, ids=lambda w: w.name)
+@pytest.mark.parametrize("w", BIG_OPS, ids=lambda w: w.name)
 def test_full_size_single_operators(w):
     ell, p, Y = inputs.make_case(w)
     Y = f32(Y)
