@@ -339,30 +339,36 @@ __device__ __forceinline__ void tile_ramp(const SliceDesc &s, int arg, int tile,
         for (int j = threadIdx.x; j < nb; j += AIR_THREADS) dst[off + j] = src[off + j];
         return;
     }
-    // P[PO + k] = Y[k] for 0 <= k < nb, zero elsewhere.  The windows reach
+    // P(PO + k) = Y[k] for 0 <= k < nb, zero elsewhere.  The windows reach
     // from j - (nb-1) - 2 (the prefetch after the last tap) to
     // j + RAMP_R + nb, so the padding is nb + 2 on the left and nb + R + 4 on
-    // the right of any output j < nb.
+    // the right of any output j < nb.  P is stored de-interleaved by residue
+    // mod 4, P(k) at (k & 3) * PQ + (k >> 2): a thread owns RAMP_R = 4
+    // consecutive outputs, so in every load all threads of a warp share the
+    // residue and read consecutive words (no bank conflicts).
     const int PO = nb + 2;
     const int plen = 3 * nb + 2 * RAMP_R + 4;
-    float *P = sm, *tp = sm + plen;
+    const int PQ = (plen + 3) >> 2;
+    float *P = sm, *tp = sm + 4 * PQ;
     const float *__restrict__ pw = s.prew;
     for (int k = threadIdx.x; k < plen; k += AIR_THREADS) {
         const int i = k - PO;
-        P[k] = (i >= 0 && i < nb) ? (pw ? src[off + i] * __ldg(pw + i) : src[off + i]) : 0.f;
+        P[(k & 3) * PQ + (k >> 2)] = (i >= 0 && i < nb) ? (pw ? src[off + i] * __ldg(pw + i) : src[off + i]) : 0.f;
     }
     for (int k = threadIdx.x; k < nb; k += AIR_THREADS) tp[k] = __ldg(s.taps + k);
     __syncthreads();
     const float diag = s.ramp_diag;
 #pragma unroll 1
     for (int j0 = threadIdx.x * RAMP_R; j0 < nb; j0 += AIR_THREADS * RAMP_R) {
-        const float *c = P + PO + j0;
+        // value at output offset o from j0: P(PO + j0 + o); j0 is a multiple of 4
+        const int jq = j0 >> 2;
+        auto at = [&](int o) { const int k = PO + o; return P[(k & 3) * PQ + (k >> 2) + jq]; };
         float ctr[RAMP_R], L[RAMP_R], R[RAMP_R], acc[RAMP_R];
 #pragma unroll
         for (int i = 0; i < RAMP_R; ++i) {
-            ctr[i] = c[i];
-            L[i] = c[i - 1];          // Y[j - m], m = 1
-            R[i] = c[i + 1];          // Y[j + m], m = 1
+            ctr[i] = at(i);
+            L[i] = at(i - 1);          // Y[j - m], m = 1
+            R[i] = at(i + 1);          // Y[j + m], m = 1
             acc[i] = 0.f;
         }
 #pragma unroll 2
@@ -374,12 +380,12 @@ __device__ __forceinline__ void tile_ramp(const SliceDesc &s, int arg, int tile,
             // slide to m + 2: left window moves down by two, right window up by two
 #pragma unroll
             for (int i = RAMP_R - 1; i >= 2; --i) L[i] = L[i - 2];
-            L[1] = c[-m - 1];
-            L[0] = c[-m - 2];
+            L[1] = at(-m - 1);
+            L[0] = at(-m - 2);
 #pragma unroll
             for (int i = 0; i < RAMP_R - 2; ++i) R[i] = R[i + 2];
-            R[RAMP_R - 2] = c[RAMP_R - 2 + m + 2];
-            R[RAMP_R - 1] = c[RAMP_R - 1 + m + 2];
+            R[RAMP_R - 2] = at(RAMP_R - 2 + m + 2);
+            R[RAMP_R - 1] = at(RAMP_R - 1 + m + 2);
         }
 #pragma unroll
         for (int i = 0; i < RAMP_R; ++i)
@@ -766,7 +772,7 @@ __device__ __forceinline__ void tile_framelet(const SliceDesc &s, int adjoint, i
 // Dynamic shared memory (bytes) a tile of `op` needs for a slice.
 __host__ inline size_t tile_smem(const SliceDesc &s, int op) {
     switch (op) {
-    case OP_RAMP: return sizeof(float) * (4 * (size_t)s.nb + 2 * RAMP_R + 4);
+    case OP_RAMP: return sizeof(float) * (4 * (size_t)((3 * s.nb + 2 * RAMP_R + 4 + 3) / 4) + (size_t)s.nb);
     case OP_SHRINK: case OP_PROX: return sizeof(float) * SHR_SMEM_FLOATS;
     case OP_FRAMELET: case OP_FRAMELET_T: return sizeof(float) * 9 * SHR_H * SHR_H;
     case OP_TRANSPOSE: return sizeof(float) * 32 * 33;
