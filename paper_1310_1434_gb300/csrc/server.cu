@@ -78,6 +78,11 @@ struct air_server {
     Task *h_tasks = nullptr;             // pinned [RING][max_slots]
     cudaEvent_t ring_ev[RING] = {};
     int ring_pos = 0;
+    // side streams the tensor-core filters of a step fork onto (each is a
+    // small GEMM that fills part of the GPU alone), joined back by events
+    static constexpr int TC_SIDE = 8;
+    cudaStream_t side[TC_SIDE] = {};
+    cudaEvent_t fork = nullptr, join[TC_SIDE] = {};
     std::vector<int> free_slots;
 
     double now() const {
@@ -202,13 +207,25 @@ air_status enqueue_step(air_server *S) {
     }
     if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("server step: ") + cudaGetErrorString(e));
     auto it = by_op.find(OP_RAMP_TC);
-    if (it != by_op.end())
-        for (Request *r : it->second) {
+    if (it != by_op.end()) {
+        const int nside = (int)std::min<size_t>(air_server::TC_SIDE, it->second.size());
+        e = cudaEventRecord(S->fork, S->stream);
+        for (int q = 0; q < nside && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(S->side[q], S->fork, 0);
+        if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("server step: ") + cudaGetErrorString(e));
+        air_status st = AIR_OK;
+        for (size_t q = 0; q < it->second.size() && st == AIR_OK; ++q) {
+            Request *r = it->second[q];
             const SliceDesc &sd = S->h_slices[r->slot];
             const int arg = r->prog[r->pc].arg;
-            air_status st = ramp_tc_apply(r->plan, arg == RSRC_Y ? sd.y : sd.z, sd.zc, sd.cg, arg == RSRC_Z, S->stream);
-            if (st != AIR_OK) return st;
+            st = ramp_tc_apply(r->plan, arg == RSRC_Y ? sd.y : sd.z, sd.zc, sd.cg, arg == RSRC_Z,
+                               S->side[q % air_server::TC_SIDE]);
         }
+        for (int q = 0; q < nside; ++q) {        // join even after a failure: the stream stays ordered
+            cudaEventRecord(S->join[q], S->side[q]);
+            cudaStreamWaitEvent(S->stream, S->join[q], 0);
+        }
+        if (st != AIR_OK) return st;
+    }
     cudaEventRecord(S->ring_ev[k], S->stream);
     // advance; a request past its last phase copies its image out
     for (Request *r : S->active) {
@@ -289,6 +306,11 @@ extern "C" air_status air_server_create(size_t hbm_budget_bytes, int max_slots, 
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_slices, sizeof(SliceDesc) * max_slots);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_tasks, sizeof(Task) * max_slots * RING);
     for (int k = 0; k < RING && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&S->ring_ev[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->fork, cudaEventDisableTiming);
+    for (int q = 0; q < air_server::TC_SIDE && e == cudaSuccess; ++q) {
+        e = cudaStreamCreateWithFlags(&S->side[q], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->join[q], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(AIR_ERR_CUDA, std::string("server creation: ") + cudaGetErrorString(e));
@@ -406,6 +428,11 @@ extern "C" air_status air_server_destroy(air_server *S) {
     }
     for (int k = 0; k < RING; ++k)
         if (S->ring_ev[k]) cudaEventDestroy(S->ring_ev[k]);
+    for (int q = 0; q < air_server::TC_SIDE; ++q) {
+        if (S->side[q]) cudaStreamDestroy(S->side[q]);
+        if (S->join[q]) cudaEventDestroy(S->join[q]);
+    }
+    if (S->fork) cudaEventDestroy(S->fork);
     cudaFree(S->d_slices);
     cudaFree(S->d_tasks);
     cudaFreeHost(S->h_slices);
