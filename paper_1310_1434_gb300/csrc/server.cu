@@ -78,8 +78,8 @@ struct air_server {
     Task *h_tasks = nullptr;             // pinned [RING][max_slots]
     cudaEvent_t ring_ev[RING] = {};
     int ring_pos = 0;
-    // side streams the tensor-core filters of a step fork onto (each is a
-    // small GEMM that fills part of the GPU alone), joined back by events
+    // side streams the independent launches of a step fork onto, joined
+    // back by events before the step's ring event
     static constexpr int TC_SIDE = 8;
     cudaStream_t side[TC_SIDE] = {};
     cudaEvent_t fork = nullptr, join[TC_SIDE] = {};
@@ -199,33 +199,40 @@ air_status enqueue_step(air_server *S) {
         l.n = nt - l.off;
         if (l.n > 0) launches.push_back(l);
     }
+    // The requests of a step are at different phases (they arrived at
+    // different times), so a step is one grouped launch per op present, each
+    // over few requests, plus a tensor-core filter per BF16X3 request in a
+    // filter phase.  Every request is in exactly one of them, so they are
+    // independent: they fork onto the side streams and run concurrently, and
+    // the step's ring event follows the join.
     cudaError_t e = cudaSuccess;
     if (nt > 0) e = cudaMemcpyAsync(dt, ht, nt * sizeof(Task), cudaMemcpyHostToDevice, S->stream);
-    for (const L &l : launches) {
-        if (e != cudaSuccess) break;
-        e = launch_group(l.op, S->d_slices, dt + l.off, l.n, l.tiles, l.smem, S->stream);
-    }
-    if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("server step: ") + cudaGetErrorString(e));
     auto it = by_op.find(OP_RAMP_TC);
-    if (it != by_op.end()) {
-        const int nside = (int)std::min<size_t>(air_server::TC_SIDE, it->second.size());
-        e = cudaEventRecord(S->fork, S->stream);
-        for (int q = 0; q < nside && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(S->side[q], S->fork, 0);
-        if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("server step: ") + cudaGetErrorString(e));
-        air_status st = AIR_OK;
-        for (size_t q = 0; q < it->second.size() && st == AIR_OK; ++q) {
-            Request *r = it->second[q];
-            const SliceDesc &sd = S->h_slices[r->slot];
-            const int arg = r->prog[r->pc].arg;
-            st = ramp_tc_apply(r->plan, arg == RSRC_Y ? sd.y : sd.z, sd.zc, sd.cg, arg == RSRC_Z,
-                               S->side[q % air_server::TC_SIDE]);
+    const size_t ntc = it != by_op.end() ? it->second.size() : 0;
+    const int nside = (int)std::min<size_t>(air_server::TC_SIDE, launches.size() + ntc);
+    if (e == cudaSuccess) e = cudaEventRecord(S->fork, S->stream);
+    for (int q = 0; q < nside && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(S->side[q], S->fork, 0);
+    if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("server step: ") + cudaGetErrorString(e));
+    int q = 0;
+    air_status st = AIR_OK;
+    for (const L &l : launches) {
+        e = launch_group(l.op, S->d_slices, dt + l.off, l.n, l.tiles, l.smem, S->side[q++ % nside]);
+        if (e != cudaSuccess) {
+            st = fail(AIR_ERR_CUDA, std::string("server step: ") + cudaGetErrorString(e));
+            break;
         }
-        for (int q = 0; q < nside; ++q) {        // join even after a failure: the stream stays ordered
-            cudaEventRecord(S->join[q], S->side[q]);
-            cudaStreamWaitEvent(S->stream, S->join[q], 0);
-        }
-        if (st != AIR_OK) return st;
     }
+    for (size_t i = 0; i < ntc && st == AIR_OK; ++i) {
+        Request *r = it->second[i];
+        const SliceDesc &sd = S->h_slices[r->slot];
+        const int arg = r->prog[r->pc].arg;
+        st = ramp_tc_apply(r->plan, arg == RSRC_Y ? sd.y : sd.z, sd.zc, sd.cg, arg == RSRC_Z, S->side[q++ % nside]);
+    }
+    for (int k2 = 0; k2 < nside; ++k2) {       // join even after a failure: the stream stays ordered
+        cudaEventRecord(S->join[k2], S->side[k2]);
+        cudaStreamWaitEvent(S->stream, S->join[k2], 0);
+    }
+    if (st != AIR_OK) return st;
     cudaEventRecord(S->ring_ev[k], S->stream);
     // advance; a request past its last phase copies its image out
     for (Request *r : S->active) {

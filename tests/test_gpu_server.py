@@ -56,7 +56,9 @@ def test_results_alone_equal_results_in_the_mix():
 
 
 def test_overlap_and_timing_records():
-    ws = [mix()[i] for i in (1, 2, 0)]          # the longest first
+    # long enough (10 x 4 iterations) that submitting all three takes far less
+    # time than any one solve; the longest first
+    ws = [dataclasses.replace(mix()[i], n_outer=10, n_cg=4) for i in (1, 2, 0)]
     Ys = [inputs.make_case(w)[2].astype(np.float32).ravel() for w in ws]
     srv = air.Server(8 * GB, max_slots=16)
     # warm the plan pool, so that admission below is a pool lookup, not a plan
