@@ -225,6 +225,14 @@ AIR_API air_status air_solve_host(const air_plan *plan, const float *Y_host, flo
 AIR_API air_status air_solve_batch(int n, air_plan *const *plans, const float *const *Y,
                            const float *lambda, const float *mu, const int *n_outer,
                            const int *n_cg, float *const *X, air_stream stream);
+/* air_solve_batch from and to HOST memory: Y_host[i] (n_views*n_bins floats)
+ * is copied into plan i's staging buffer, the batch is solved there (the
+ * staging buffers are fixed per plan, so repeated calls replay one captured
+ * graph), and X_host[i] (n*n floats) receives the image.  Pinned host memory
+ * makes the copies asynchronous.  Returns after the images are on the host. */
+AIR_API air_status air_solve_batch_host(int n, air_plan *const *plans, const float *const *Y_host,
+                                        const float *lambda, const float *mu, const int *n_outer,
+                                        const int *n_cg, float *const *X_host, air_stream stream);
 /* The same batch in ONE persistent cooperative kernel launch (captured in a
  * CUDA graph) whose blocks run every phase of every slice, separated by a
  * grid barrier with a bounded wait (AIR_ERR_TIMEOUT if it gives up).  FP32

@@ -31,8 +31,10 @@ EXPORTS = ["air_last_error", "air_plan_create", "air_plan_destroy", "air_plan_by
            "air_project",
            "air_filter", "air_backproject", "air_filtered_backproject", "air_filtered_backproject_noalloc",
            "air_framelet", "air_shrink",
-           "air_solve", "air_solve_l2", "air_solve_fbs", "air_fbp", "air_solve_host", "air_solve_batch", "air_solve_batch_persistent", "air_server_create", "air_server_submit",
-           "air_server_poll", "air_server_wait", "air_server_times", "air_server_destroy"]
+           "air_solve", "air_solve_l2", "air_solve_fbs", "air_fbp", "air_solve_host",
+           "air_solve_batch", "air_solve_batch_host", "air_solve_batch_persistent",
+           "air_server_create", "air_server_submit", "air_server_poll", "air_server_wait", "air_server_times",
+           "air_server_destroy"]
 
 
 class AirError(RuntimeError):
@@ -91,6 +93,7 @@ def load(build_if_missing: bool = False):
         "air_solve_fbs": (i32, [P, P, f32, f32, i32, P, P]),
         "air_solve_batch": (i32, [i32, P, P, P, P, P, P, P, P]),
         "air_solve_batch_persistent": (i32, [i32, P, P, P, P, P, P, P, P]),
+        "air_solve_batch_host": (i32, [i32, P, P, P, P, P, P, P, P]),
         "air_server_create": (i32, [ctypes.c_size_t, i32, ctypes.POINTER(P)]),
         "air_server_submit": (i32, [P, g, P, f32, f32, i32, i32, ctypes.POINTER(u64)]),
         "air_server_poll": (i32, [P, u64, P]),
@@ -283,6 +286,13 @@ def _batch(fn, name, plans, Ys, lams, mus, n_outers, n_cgs, Xs, stream):
 
 def air_solve_batch(plans, Ys, lams, mus, n_outers, n_cgs, Xs, stream=None):
     _batch(load().air_solve_batch, "air_solve_batch", plans, Ys, lams, mus, n_outers, n_cgs, Xs, stream)
+
+
+def air_solve_batch_host(plans, Ys_host, lams, mus, n_outers, n_cgs, Xs_host, stream=None):
+    """Ys_host / Xs_host: host arrays (numpy or CPU tensors, float32, contiguous;
+    pinned memory makes the copies asynchronous)."""
+    _batch(load().air_solve_batch_host, "air_solve_batch_host", plans, Ys_host, lams, mus, n_outers, n_cgs,
+           Xs_host, stream)
 
 
 def air_solve_batch_persistent(plans, Ys, lams, mus, n_outers, n_cgs, Xs, stream=None):

@@ -245,6 +245,35 @@ extern "C" air_status air_solve_batch(int n, air_plan *const *plans, const float
     return run_cached(G, st);
 }
 
+extern "C" air_status air_solve_batch_host(int n, air_plan *const *plans, const float *const *Y_host,
+                                           const float *lambda, const float *mu, const int *n_outer,
+                                           const int *n_cg, float *const *X_host, air_stream stream) {
+    if (n < 1 || n > 4096) return fail(AIR_ERR_INVALID_ARG, "n must be in 1..4096");
+    if (!plans || !Y_host || !X_host) return fail(AIR_ERR_INVALID_ARG, "NULL array argument");
+    const cudaStream_t st = (cudaStream_t)stream;
+    std::vector<const float *> Yd(n);
+    std::vector<float *> Xd(n);
+    for (int i = 0; i < n; ++i) {
+        if (!plans[i]) return fail(AIR_ERR_INVALID_ARG, "plan is NULL");
+        if (!Y_host[i] || !X_host[i]) return fail(AIR_ERR_INVALID_ARG, "Y_host[i] and X_host[i] must not be NULL");
+        const size_t sino = (size_t)plans[i]->geom.n_views * plans[i]->geom.n_bins * 4;
+        const cudaError_t e = cudaMemcpyAsync(plans[i]->ybuf, Y_host[i], sino, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("batch copy-in: ") + cudaGetErrorString(e));
+        Yd[i] = plans[i]->ybuf;
+        Xd[i] = plans[i]->xbuf;
+    }
+    air_status s = air_solve_batch(n, plans, Yd.data(), lambda, mu, n_outer, n_cg, Xd.data(), stream);
+    if (s != AIR_OK) return s;
+    for (int i = 0; i < n; ++i) {
+        const size_t img = (size_t)plans[i]->geom.n * plans[i]->geom.n * 4;
+        const cudaError_t e = cudaMemcpyAsync(X_host[i], plans[i]->xbuf, img, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("batch copy-out: ") + cudaGetErrorString(e));
+    }
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("batch copy-out: ") + cudaGetErrorString(e));
+    return AIR_OK;
+}
+
 extern "C" air_status air_solve_batch_persistent(int n, air_plan *const *plans, const float *const *Y,
                                                  const float *lambda, const float *mu, const int *n_outer,
                                                  const int *n_cg, float *const *X, air_stream stream) {

@@ -96,3 +96,20 @@ def test_config2_batch_of_64_uneven_slices():
             og = oracle.Geometry(**{k: getattr(w.geom, k) for k in oracle.Geometry.__dataclass_fields__})
             ref = oracle.solve(og, Y.cpu().numpy().astype(np.float64), w.lam, w.mu, w.n_outer, w.n_cg)
             assert np.linalg.norm(a - ref.ravel()) <= 1e-4 * np.linalg.norm(ref), w.name
+
+
+def test_host_buffer_batch_equals_device_batch():
+    ws = cases()
+    Ys = [f32(inputs.make_case(w)[2]).ravel().astype(np.float32) for w in ws]
+    plans = [air.Plan(w.geom) for w in ws]
+    args = ([w.lam for w in ws], [w.mu for w in ws], [w.n_outer for w in ws], [w.n_cg for w in ws])
+    Xd = [torch.empty(w.geom.n ** 2, device=DEV) for w in ws]
+    air.air_solve_batch(plans, [torch.as_tensor(y, device=DEV) for y in Ys], *args, Xd)
+    Xh = [torch.empty(w.geom.n ** 2, pin_memory=True) for w in ws]
+    Yh = [torch.from_numpy(y).pin_memory() for y in Ys]
+    for _ in range(2):   # the second call replays the captured graph
+        for x in Xh:
+            x.fill_(float("nan"))
+        air.air_solve_batch_host(plans, Yh, *args, Xh)
+        for a, b in zip(Xh, Xd):
+            assert torch.equal(a, b.cpu())
