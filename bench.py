@@ -375,11 +375,14 @@ def main():
     def step():
         air.air_solve_batch(plans, Yd, lam, mu, no, ncg, Xd)
 
-    # kernels per step: one grouped launch per phase of the common program,
-    # plus two tensor-core filter kernels per slice per filter phase
-    n_ph_outer = 5 + 7 * ws[0].n_cg + 1
-    n_filter = 1 + ws[0].n_outer * (1 + ws[0].n_cg)
-    launches_per_step = (4 + ws[0].n_outer * n_ph_outer - n_filter) + 2 * B * n_filter
+    # kernels per step: one grouped launch per phase of the common program
+    # (5 setup phases, 7 per CG iteration, a shrink per outer step and a CG
+    # restart between outer steps), the filter phases instead as two
+    # tensor-core kernels per slice
+    n_out, n_cgi = ws[0].n_outer, ws[0].n_cg
+    n_phases = 5 + n_out * (7 * n_cgi + 1) + (n_out - 1)
+    n_filter = 1 + n_out * n_cgi
+    launches_per_step = (n_phases - n_filter) + 2 * B * n_filter
 
     for _ in range(max(3, args.warmup)):
         step()

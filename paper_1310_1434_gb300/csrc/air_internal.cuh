@@ -38,6 +38,7 @@ enum Op : int {
     OP_AXPY,       // q = x + step r            (forward step of Eq. 6, r = A'^T(Y - A x))
     OP_PROX,       // x = W^T S_tau(W q)        (framelet proximal step)
     OP_FBP,        // ext_out = fan-beam FBP weighted backprojection of zc
+    OP_RESTART,    // CG restart of an outer step: r = rhs0 (arg -1) or r += mu (g_new - g_old); p = r; rho
     OP_COUNT
 };
 
@@ -117,6 +118,7 @@ struct SliceDesc {
     float fbp_scale;     // dbeta / dx^2
     // solver state (plan-owned workspace)
     float *x, *r, *p, *q, *rhs0, *g;   // n*n
+    float *g2;                         // n*n: g of the previous outer step (g is double-buffered)
     float *xp, *xt;                    // n*(n+2) each: zero-padded copy and transpose of the projector's input
     float *bwd_part;                   // bwd_parts * n*n: the backprojector's per-view-part sums
     int bwd_parts;                     // S: views split over S blocks per pixel tile (tuned)
@@ -169,7 +171,7 @@ __host__ __device__ inline int tiles_of(const SliceDesc &s, int op) {
     case OP_FWD: return tiles_fwd(s);
     case OP_RAMP: return tiles_ramp(s);
     case OP_BWD: return tiles_bwd(s);
-    case OP_CG_A: case OP_CG_B: case OP_ZERO: case OP_BWD_FIN: case OP_AXPY: return tiles_vec(s);
+    case OP_CG_A: case OP_CG_B: case OP_ZERO: case OP_BWD_FIN: case OP_AXPY: case OP_RESTART: return tiles_vec(s);
     case OP_SHRINK: case OP_FRAMELET: case OP_FRAMELET_T: case OP_TRANSPOSE: case OP_PROX: case OP_FBP:
         return tiles_shr(s);
     default: return 0;

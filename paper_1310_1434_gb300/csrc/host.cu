@@ -101,7 +101,7 @@ size_t plan_bytes_estimate(const air_geometry &g) {
     const size_t nn = (size_t)g.n * g.n, rays = (size_t)g.n_views * g.n_bins;
     const size_t parts = (size_t)choose_bwd_parts(s);
     size_t b = rays * sizeof(RayFx) + (size_t)g.n_views * tiles_bwd_xy(s) * 4 + (size_t)g.n_bins * 4;
-    b += nn * 4 * (6 + 2 * parts + 18 + 1);      // x r p q rhs0 g, parts (up to 2x), b b2, xbuf
+    b += nn * 4 * (7 + 2 * parts + 18 + 1);      // x r p q rhs0 g g', parts (up to 2x), b b2, xbuf
     b += (size_t)g.n * (g.n + 2) * 4 * 2;        // xp xt
     b += (size_t)g.n_views * 8 + (size_t)g.n_bins * 8;   // FBP tables
     b += rays * 4 * 3;                           // z zc ybuf
@@ -465,7 +465,7 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     const int parts_max = std::min(V, 2 * s.bwd_parts);
     // carve one allocation
     struct Piece { void **dst; size_t bytes; };
-    float *x, *r, *p, *q, *rhs0, *gg, *b, *b2, *z, *zc, *ybuf, *xbuf, *xp, *xt, *bpart;
+    float *x, *r, *p, *q, *rhs0, *gg, *gg2, *b, *b2, *z, *zc, *ybuf, *xbuf, *xp, *xt, *bpart;
     const size_t npad = (size_t)n * (n + 2);   // padded copies of the projector's input
     RayFx *ray;
     unsigned *vt;
@@ -482,7 +482,7 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
         {(void **)&taps, (size_t)nb * sizeof(float)}, {(void **)&fview, (size_t)V * sizeof(float2)},
         {(void **)&fbw, (size_t)nb * sizeof(float)}, {(void **)&fbt, (size_t)nb * sizeof(float)},
         {(void **)&x, nn * 4}, {(void **)&r, nn * 4}, {(void **)&p, nn * 4}, {(void **)&q, nn * 4},
-        {(void **)&rhs0, nn * 4}, {(void **)&gg, nn * 4}, {(void **)&b, 9 * nn * 4}, {(void **)&b2, 9 * nn * 4},
+        {(void **)&rhs0, nn * 4}, {(void **)&gg, nn * 4}, {(void **)&gg2, nn * 4}, {(void **)&b, 9 * nn * 4}, {(void **)&b2, 9 * nn * 4},
         {(void **)&z, rays * 4}, {(void **)&zc, rays * 4}, {(void **)&ybuf, rays * 4}, {(void **)&xbuf, nn * 4},
         {(void **)&cg, sizeof(CgState)}, {(void **)&partial, npart * sizeof(double)}};
     size_t total = 0;
@@ -535,7 +535,7 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     s.fbp_w = fbw;
     s.fbp_taps = fbt;
     s.taps = taps;
-    s.x = x; s.r = r; s.p = p; s.q = q; s.rhs0 = rhs0; s.g = gg; s.b = b; s.b2 = b2; s.xp = xp; s.xt = xt;
+    s.x = x; s.r = r; s.p = p; s.q = q; s.rhs0 = rhs0; s.g = gg; s.g2 = gg2; s.b = b; s.b2 = b2; s.xp = xp; s.xt = xt;
     s.bwd_part = bpart;
     s.z = z; s.zc = zc; s.y = ybuf;
     s.cg = cg;
@@ -744,19 +744,19 @@ extern "C" air_status air_shrink(const air_plan *P, const float *X, float *b, fl
 namespace air {
 
 // The split-Bregman program of one slice as a list of phases.
+// The split-Bregman program of one slice (Methods, Eq. 5 and ref. [24]).
+// Each outer step's CG restarts from the residual the previous CG left,
+// corrected for the change of the right-hand side (OP_RESTART): CG keeps
+// r = b - M X, and b changes between outer steps only by mu (g_new - g_old).
 std::vector<Phase> solve_program(int n_outer, int n_cg, bool tc_ramp) {
     std::vector<Phase> prog;
     const int ramp = tc_ramp ? OP_RAMP_TC : OP_RAMP;
     prog.push_back({ramp, RSRC_Y});        // zc = C y
     prog.push_back({OP_BWD, BWD_RHS0});   // rhs0 = A^T zc
     prog.push_back({OP_BWD_FIN, BWD_RHS0});
-    prog.push_back({OP_ZERO, 0});         // X = 0, b = 0, g = 0
+    prog.push_back({OP_ZERO, 0});         // X = 0, b = 0, g = g' = 0
+    prog.push_back({OP_RESTART, -1});     // r = p = rhs0 (X = 0, g = 0)
     for (int k = 0; k < n_outer; ++k) {
-        prog.push_back({OP_TRANSPOSE, SRC_X});        // r = rhs0 + mu g - M x, p = r
-        prog.push_back({OP_FWD, SRC_X});
-        prog.push_back({ramp, RSRC_Z});
-        prog.push_back({OP_BWD, BWD_RESID});
-        prog.push_back({OP_BWD_FIN, BWD_RESID});
         for (int i = 0; i < n_cg; ++i) {
             prog.push_back({OP_TRANSPOSE, SRC_P});    // q = M p
             prog.push_back({OP_FWD, SRC_P});
@@ -767,6 +767,7 @@ std::vector<Phase> solve_program(int n_outer, int n_cg, bool tc_ramp) {
             prog.push_back({OP_CG_B, 0});
         }
         prog.push_back({OP_SHRINK, k & 1});
+        if (k + 1 < n_outer) prog.push_back({OP_RESTART, k & 1});   // r += mu (g_k - g_{k-1})
     }
     return prog;
 }

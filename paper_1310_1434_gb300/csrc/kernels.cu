@@ -32,10 +32,11 @@ __global__ void __launch_bounds__(AIR_THREADS) k_op(const SliceDesc s, int arg) 
         tile_prox(s, tile, sm);
     } else if constexpr (OP == OP_FBP) {
         tile_fbp(s, tile);
+    } else if constexpr (OP == OP_RESTART) {
+        tile_restart(s, arg, tile);
     } else if constexpr (OP == OP_SHRINK) {
         if (arg < 2) {
-            ShrinkArgs a{s.x, arg ? s.b2 : s.b, arg ? s.b : s.b2, s.g, s.tau};
-            tile_shrink(s, a, tile, true, nullptr, sm);
+            run_shrink(s, arg, tile, sm);
         } else {  // stand-alone call: X, b (read), scratch b', g from the ext operands
             ShrinkArgs a{s.ext_in, s.ext_out, s.b2, s.ext_out2, s.tau};
             tile_shrink(s, a, tile, true, s.ext_scalar, sm);
@@ -79,6 +80,7 @@ cudaError_t launch_op(int op, const SliceDesc &s, int arg, cudaStream_t st) {
     case OP_AXPY: return launch_one<OP_AXPY>(s, arg, st);
     case OP_PROX: return launch_one<OP_PROX>(s, arg, st);
     case OP_FBP: return launch_one<OP_FBP>(s, arg, st);
+    case OP_RESTART: return launch_one<OP_RESTART>(s, arg, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -147,10 +149,8 @@ k_group(const SliceDesc *__restrict__ slices, const Task *__restrict__ tasks, in
     else if constexpr (OP == OP_AXPY) tile_axpy(s, tile);
     else if constexpr (OP == OP_PROX) tile_prox(s, tile, sm);
     else if constexpr (OP == OP_TRANSPOSE) tile_transpose(s, t.arg, tile, sm);
-    else if constexpr (OP == OP_SHRINK) {
-        ShrinkArgs a{s.x, t.arg ? s.b2 : s.b, t.arg ? s.b : s.b2, s.g, s.tau};
-        tile_shrink(s, a, tile, true, nullptr, sm);
-    }
+    else if constexpr (OP == OP_SHRINK) run_shrink(s, t.arg, tile, sm);
+    else if constexpr (OP == OP_RESTART) tile_restart(s, t.arg, tile);
 }
 
 template <int OP>
@@ -181,6 +181,7 @@ cudaError_t launch_group(int op, const SliceDesc *d_slices, const Task *d_tasks,
     case OP_SHRINK: return launch_group_op<OP_SHRINK>(d_slices, d_tasks, ntasks, total_tiles, smem, st);
     case OP_AXPY: return launch_group_op<OP_AXPY>(d_slices, d_tasks, ntasks, total_tiles, smem, st);
     case OP_PROX: return launch_group_op<OP_PROX>(d_slices, d_tasks, ntasks, total_tiles, smem, st);
+    case OP_RESTART: return launch_group_op<OP_RESTART>(d_slices, d_tasks, ntasks, total_tiles, smem, st);
     default: return cudaErrorInvalidValue;
     }
 }

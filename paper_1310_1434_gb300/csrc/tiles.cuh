@@ -495,6 +495,38 @@ __device__ __forceinline__ void tile_cg_b(const SliceDesc &s, int tile) {
     }
 }
 
+// The CG restart of an outer split-Bregman step.  CG keeps r = b - M x, so
+// when the right-hand side b = A'^T Y + mu W^T(d - b') changes only by
+// mu (g_new - g_old) between outer steps, the new residual is
+// r + mu (g_new - g_old) with no operator application; at X = 0 it is
+// A'^T Y.  arg = -1: r = rhs0; arg = parity of the outer step that just
+// shrank (its g went to g2 if odd, g if even): r += mu (g_new - g_old).
+// Then p = r and rho = r.r (FP64), and the CG restarts unless rho = 0.
+__device__ __forceinline__ void tile_restart(const SliceDesc &s, int arg, int tile) {
+    __shared__ double sh[AIR_THREADS / 32];
+    const int nn = s.n * s.n;
+    const int base = tile * VEC_PER_TILE;
+    const float *gn = arg == 1 ? s.g2 : s.g, *go = arg == 1 ? s.g : s.g2;
+    double part = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = base + k * AIR_THREADS + threadIdx.x;
+        if (i < nn) {
+            const float rv = arg < 0 ? s.rhs0[i] : fmaf(s.mu, gn[i] - go[i], s.r[i]);
+            s.r[i] = rv;
+            s.p[i] = rv;
+            part += (double)rv * (double)rv;
+        }
+    }
+    part = block_sum(part, sh);
+    double tot;
+    if (reduce_tiles(s, tile, tiles_vec(s), part, sh, &tot) && threadIdx.x == 0) {
+        CgState *c = s.cg;
+        c->rho = tot;
+        c->stop = !(tot != 0.0);
+    }
+}
+
 // q = x + step r: the forward step of forward-backward splitting (Eq. 6),
 // with r = A'^T (Y - A x) from the OP_BWD_FIN residual epilogue at mu = 0.
 __device__ __forceinline__ void tile_axpy(const SliceDesc &s, int tile) {
@@ -516,6 +548,7 @@ __device__ __forceinline__ void tile_zero(const SliceDesc &s, int tile) {
         if (i < nn) {
             s.x[i] = 0.f;
             s.g[i] = 0.f;
+            s.g2[i] = 0.f;
 #pragma unroll
             for (int band = 0; band < 9; ++band) s.b[(size_t)band * nn + i] = 0.f;
         }
@@ -781,6 +814,14 @@ __host__ inline size_t tile_smem(const SliceDesc &s, int op) {
     }
 }
 
+// The shrink of outer step k of the solver, arg = k & 1: the Bregman
+// variable goes b -> b2 on even steps and b2 -> b on odd ones, and g to g on
+// even steps and to g2 on odd ones (the restart needs the previous g).
+__device__ __forceinline__ void run_shrink(const SliceDesc &s, int arg, int tile, float *sm) {
+    ShrinkArgs a{s.x, arg ? s.b2 : s.b, arg ? s.b : s.b2, arg ? s.g2 : s.g, s.tau};
+    tile_shrink(s, a, tile, true, nullptr, sm);
+}
+
 // One tile of any op (used by the task-table and persistent kernels).
 __device__ __forceinline__ void run_tile(const SliceDesc &s, int op, int arg, int tile, float *sm) {
     switch (op) {
@@ -795,11 +836,8 @@ __device__ __forceinline__ void run_tile(const SliceDesc &s, int op, int arg, in
     case OP_AXPY: tile_axpy(s, tile); break;
     case OP_PROX: tile_prox(s, tile, sm); break;
     case OP_FBP: tile_fbp(s, tile); break;
-    case OP_SHRINK: {   // arg = parity of the outer step: b -> b2, then b2 -> b
-        ShrinkArgs a{s.x, arg ? s.b2 : s.b, arg ? s.b : s.b2, s.g, s.tau};
-        tile_shrink(s, a, tile, true, nullptr, sm);
-        break;
-    }
+    case OP_SHRINK: run_shrink(s, arg, tile, sm); break;
+    case OP_RESTART: tile_restart(s, arg, tile); break;
     default: break;
     }
 }
