@@ -63,6 +63,7 @@ struct air_server {
     int device = 0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
+    std::atomic<int> waiters{0};     // API calls waiting for `mu` (the worker lets them in)
     std::deque<Request *> queue;
     std::vector<Request *> active;
     std::map<uint64_t, std::unique_ptr<Request>> all;
@@ -83,6 +84,13 @@ struct air_server {
     static constexpr int TC_SIDE = 8;
     cudaStream_t side[TC_SIDE] = {};
     cudaEvent_t fork = nullptr, join[TC_SIDE] = {};
+    // pinned host staging buffers of finished requests, by size, reused by
+    // later submissions (pinning memory costs milliseconds per call)
+    std::mutex pin_mu;
+    std::multimap<size_t, float *> pin_pool;
+    size_t pin_pooled = 0;
+    std::vector<cudaEvent_t> ev_pool;    // completion events of finished requests (also under pin_mu)
+    static constexpr size_t PIN_POOL_MAX = size_t(2) << 30;
     std::vector<int> free_slots;
 
     double now() const {
@@ -91,6 +99,47 @@ struct air_server {
 };
 
 namespace {
+
+// Takes the server lock for an API call, counted so that the worker, which
+// retakes the lock after every step, yields to it instead of starving it.
+struct ApiLock {
+    air_server *S;
+    std::unique_lock<std::mutex> lock;
+    explicit ApiLock(air_server *s) : S(s) {
+        S->waiters.fetch_add(1);
+        lock = std::unique_lock<std::mutex>(S->mu);
+        S->waiters.fetch_sub(1);
+    }
+};
+
+// A pinned host buffer of `bytes` from the pool, or a new one.
+cudaError_t pin_take(air_server *S, size_t bytes, float **out) {
+    {
+        std::lock_guard<std::mutex> lock(S->pin_mu);
+        auto it = S->pin_pool.find(bytes);
+        if (it != S->pin_pool.end()) {
+            *out = it->second;
+            S->pin_pooled -= bytes;
+            S->pin_pool.erase(it);
+            return cudaSuccess;
+        }
+    }
+    return cudaMallocHost((void **)out, bytes);
+}
+
+// Returns a pinned buffer to the pool (freed instead when the pool is full).
+void pin_give(air_server *S, size_t bytes, float *p) {
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lock(S->pin_mu);
+        if (S->pin_pooled + bytes <= air_server::PIN_POOL_MAX) {
+            S->pin_pool.emplace(bytes, p);
+            S->pin_pooled += bytes;
+            return;
+        }
+    }
+    cudaFreeHost(p);
+}
 
 // Takes an idle plan of this geometry from the pool, or creates one.
 air_status get_plan(air_server *S, const air_geometry &g, air_plan **out) {
@@ -147,6 +196,24 @@ void admit(air_server *S) {
             continue;
         }
         S->queue.pop_front();
+        if (!r->done_ev) {
+            {
+                std::lock_guard<std::mutex> lock(S->pin_mu);
+                if (!S->ev_pool.empty()) {
+                    r->done_ev = S->ev_pool.back();
+                    S->ev_pool.pop_back();
+                }
+            }
+            if (!r->done_ev) {
+                const cudaError_t ee = cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming);
+                if (ee != cudaSuccess) {
+                    r->done_ev = nullptr;
+                    put_plan(S, plan);
+                    finish(S, r, fail(AIR_ERR_CUDA, std::string("server event: ") + cudaGetErrorString(ee)));
+                    continue;
+                }
+            }
+        }
         r->plan = plan;
         r->bytes = air_plan_bytes(plan);
         S->used += r->bytes;
@@ -285,6 +352,7 @@ void worker_main(air_server *S) {
         // the active requests, and the wait on the task ring may block
         lock.unlock();
         air_status st = enqueue_step(S);
+        for (int y = 0; y < 64 && S->waiters.load() > 0; ++y) std::this_thread::yield();
         lock.lock();
         if (st != AIR_OK) {
             cudaStreamSynchronize(S->stream);
@@ -342,23 +410,24 @@ extern "C" air_status air_server_submit(air_server *S, const air_geometry *geom,
     r->mu = mu;
     r->n_outer = n_outer;
     r->n_cg = n_cg;
+    r->t[0] = S->now();              // arrival: when the caller submits
     r->bytes = plan_bytes_estimate(*geom);
     if (r->bytes > S->budget)
         return fail(AIR_ERR_BUDGET, "the request needs " + std::to_string(r->bytes) +
                                         " device bytes, more than the server's budget");
     const size_t sino = (size_t)geom->n_views * geom->n_bins * 4, img = (size_t)geom->n * geom->n * 4;
-    cudaError_t e = cudaMallocHost(&r->y_pinned, sino);
-    if (e == cudaSuccess) e = cudaMallocHost(&r->x_pinned, img);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming);
+    // no CUDA call on this path when the pools hold buffers of these sizes:
+    // the worker creates or reuses the completion event at admission
+    cudaError_t e = pin_take(S, sino, &r->y_pinned);
+    if (e == cudaSuccess) e = pin_take(S, img, &r->x_pinned);
     if (e != cudaSuccess) {
-        if (r->y_pinned) cudaFreeHost(r->y_pinned);
-        if (r->x_pinned) cudaFreeHost(r->x_pinned);
+        pin_give(S, sino, r->y_pinned);
+        pin_give(S, img, r->x_pinned);
         cudaGetLastError();
         return fail(AIR_ERR_OOM, std::string("pinned host buffers: ") + cudaGetErrorString(e));
     }
     std::memcpy(r->y_pinned, Y_host, sino);
-    r->t[0] = S->now();              // arrival: before any wait for the lock
-    std::lock_guard<std::mutex> lock(S->mu);
+    ApiLock lock(S);
     if (S->stop) return fail(AIR_ERR_INVALID_ARG, "the server is shutting down");
     r->id = S->next_id++;
     *request_id = r->id;
@@ -373,9 +442,12 @@ air_status take_result(air_server *S, std::map<uint64_t, std::unique_ptr<Request
     Request *r = it->second.get();
     const air_status st = r->status;
     if (st == AIR_OK && X_host) std::memcpy(X_host, r->x_pinned, (size_t)r->geom.n * r->geom.n * 4);
-    cudaFreeHost(r->y_pinned);
-    cudaFreeHost(r->x_pinned);
-    cudaEventDestroy(r->done_ev);
+    pin_give(S, (size_t)r->geom.n_views * r->geom.n_bins * 4, r->y_pinned);
+    pin_give(S, (size_t)r->geom.n * r->geom.n * 4, r->x_pinned);
+    if (r->done_ev) {
+        std::lock_guard<std::mutex> lock(S->pin_mu);
+        S->ev_pool.push_back(r->done_ev);
+    }
     S->all.erase(it);
     return st == AIR_OK ? AIR_OK : fail(st, "the request failed");
 }
@@ -383,7 +455,7 @@ air_status take_result(air_server *S, std::map<uint64_t, std::unique_ptr<Request
 
 extern "C" air_status air_server_poll(air_server *S, uint64_t id, float *X_host) {
     if (!S) return fail(AIR_ERR_INVALID_ARG, "server is NULL");
-    std::lock_guard<std::mutex> lock(S->mu);
+    ApiLock lock(S);
     auto it = S->all.find(id);
     if (it == S->all.end()) return fail(AIR_ERR_INVALID_ARG, "unknown request id");
     const int state = it->second->state;
@@ -393,17 +465,17 @@ extern "C" air_status air_server_poll(air_server *S, uint64_t id, float *X_host)
 
 extern "C" air_status air_server_wait(air_server *S, uint64_t id, float *X_host) {
     if (!S) return fail(AIR_ERR_INVALID_ARG, "server is NULL");
-    std::unique_lock<std::mutex> lock(S->mu);
+    ApiLock al(S);
     auto it = S->all.find(id);
     if (it == S->all.end()) return fail(AIR_ERR_INVALID_ARG, "unknown request id");
     Request *r = it->second.get();
-    S->cv_done.wait(lock, [&] { return r->state == DONE || r->state == FAILED; });
+    S->cv_done.wait(al.lock, [&] { return r->state == DONE || r->state == FAILED; });
     return take_result(S, S->all.find(id), X_host);
 }
 
 extern "C" air_status air_server_times(air_server *S, uint64_t id, double t[3]) {
     if (!S || !t) return fail(AIR_ERR_INVALID_ARG, "NULL argument");
-    std::lock_guard<std::mutex> lock(S->mu);
+    ApiLock lock(S);
     auto it = S->all.find(id);
     if (it == S->all.end()) return fail(AIR_ERR_INVALID_ARG, "unknown request id");
     const Request *r = it->second.get();
@@ -431,8 +503,10 @@ extern "C" air_status air_server_destroy(air_server *S) {
     for (auto &kv : S->all) {
         cudaFreeHost(kv.second->y_pinned);
         cudaFreeHost(kv.second->x_pinned);
-        cudaEventDestroy(kv.second->done_ev);
+        if (kv.second->done_ev) cudaEventDestroy(kv.second->done_ev);
     }
+    for (auto &pp : S->pin_pool) cudaFreeHost(pp.second);
+    for (cudaEvent_t ev : S->ev_pool) cudaEventDestroy(ev);
     for (int k = 0; k < RING; ++k)
         if (S->ring_ev[k]) cudaEventDestroy(S->ring_ev[k]);
     for (int q = 0; q < air_server::TC_SIDE; ++q) {

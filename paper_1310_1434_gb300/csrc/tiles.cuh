@@ -363,29 +363,33 @@ __device__ __forceinline__ void tile_ramp(const SliceDesc &s, int arg, int tile,
         // value at output offset o from j0: P(PO + j0 + o); j0 is a multiple of 4
         const int jq = j0 >> 2;
         auto at = [&](int o) { const int k = PO + o; return P[(k & 3) * PQ + (k >> 2) + jq]; };
+        // taps from the outermost odd lag inward: the terms grow as the lag
+        // shrinks (taps ~ 1/m^2), and summing the small ones first keeps the
+        // FP32 sum within a few ulp even for long noisy rows
+        const int mmax = (nb - 1) & 1 ? nb - 1 : nb - 2;   // largest odd lag < nb (-1: none)
         float ctr[RAMP_R], L[RAMP_R], R[RAMP_R], acc[RAMP_R];
 #pragma unroll
         for (int i = 0; i < RAMP_R; ++i) {
             ctr[i] = at(i);
-            L[i] = at(i - 1);          // Y[j - m], m = 1
-            R[i] = at(i + 1);          // Y[j + m], m = 1
+            L[i] = at(i - mmax);       // Y[j - m], m = mmax
+            R[i] = at(i + mmax);       // Y[j + m], m = mmax
             acc[i] = 0.f;
         }
 #pragma unroll 2
-        for (int m = 1; m < nb; m += 2) {
+        for (int m = mmax; m >= 1; m -= 2) {
             const float h = tp[m];
 #pragma unroll
             for (int i = 0; i < RAMP_R; ++i)
                 acc[i] = fmaf(h, __fadd_rn(__fsub_rn(L[i], ctr[i]), __fsub_rn(R[i], ctr[i])), acc[i]);
-            // slide to m + 2: left window moves down by two, right window up by two
+            // slide to m - 2: the left window moves up by two, the right down by two
 #pragma unroll
-            for (int i = RAMP_R - 1; i >= 2; --i) L[i] = L[i - 2];
-            L[1] = at(-m - 1);
-            L[0] = at(-m - 2);
+            for (int i = 0; i < RAMP_R - 2; ++i) L[i] = L[i + 2];
+            L[RAMP_R - 2] = at(RAMP_R - 2 - m + 2);
+            L[RAMP_R - 1] = at(RAMP_R - 1 - m + 2);
 #pragma unroll
-            for (int i = 0; i < RAMP_R - 2; ++i) R[i] = R[i + 2];
-            R[RAMP_R - 2] = at(RAMP_R - 2 + m + 2);
-            R[RAMP_R - 1] = at(RAMP_R - 1 + m + 2);
+            for (int i = RAMP_R - 1; i >= 2; --i) R[i] = R[i - 2];
+            R[1] = at(1 + m - 2);
+            R[0] = at(m - 2);
         }
 #pragma unroll
         for (int i = 0; i < RAMP_R; ++i)

@@ -313,3 +313,45 @@ def test_every_tuned_configuration_matches_oracle():
         air.air_plan_tune(plan, 3, 1)
     with pytest.raises(air.AirError):
         air.air_plan_tune(plan, 1, Smax + 1)
+
+
+# ------------------------------------------------------------ maximum sizes ----
+def test_maximum_image_side_projector_on_sampled_rays_and_adjoint():
+    """n = 4096, the largest image side (the ray table packs each walk range
+    in 16-bit fields): sampled rays against the oracle, one at a time, and the
+    adjoint identity of the pair over the whole image."""
+    g = inputs.Geometry(4096, 0.1, 24, 5904)
+    og = ogeom(g)
+    rng = np.random.Generator(np.random.PCG64(31))
+    X = f32(inputs.random_image(g.n, 32))
+    plan = air.Plan(g)
+    Yd = torch.empty(g.n_views * g.n_bins, device=DEV)
+    air.air_project(plan, dev(X), Yd)
+    Y = host(Yd).reshape(g.n_views, g.n_bins)
+    vs, js = rng.integers(0, g.n_views, 48), rng.integers(0, g.n_bins, 48)
+    ref = np.array([oracle.project_ray(og, X, int(v), int(j)) for v, j in zip(vs, js)])
+    got = Y[vs, js]
+    assert rel(got, ref) <= TOL_OP
+    y = f32(rng.standard_normal((g.n_views, g.n_bins)))
+    Aty = torch.empty(g.n * g.n, device=DEV)
+    air.air_backproject(plan, dev(y), Aty)
+    lhs = float(Y.ravel() @ y.ravel())
+    rhs = float(X.ravel() @ host(Aty))
+    assert abs(lhs - rhs) <= TOL_ADJ * np.linalg.norm(Y) * np.linalg.norm(y)
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16x3"])
+@pytest.mark.parametrize("kind", ["noise", "phantom"])
+def test_maximum_bin_count_filter(prec, kind):
+    """n_bins = 8192, the largest (the filter keeps a padded detector row in
+    shared memory), on white noise (no smoothness for the difference form to
+    exploit) and on phantom line integrals."""
+    g = inputs.Geometry(64, 1.0, 6, 8192, dgamma=2e-4, precision=prec)
+    if kind == "noise":
+        Y = f32(np.random.Generator(np.random.PCG64(33)).standard_normal((g.n_views, g.n_bins)))
+    else:
+        Y = f32(inputs.ellipse_line_integrals(g, inputs.random_phantom(g, 34, 6, 2)))
+    plan = air.Plan(g)
+    Zd = torch.empty(g.n_views * g.n_bins, device=DEV)
+    air.air_filter(plan, dev(Y), Zd)
+    assert rel(host(Zd), oracle.filter(ogeom(g), Y).ravel()) <= TOL_OP
