@@ -196,6 +196,91 @@ def ellipse_line_integrals(geom: Geometry, ellipses) -> np.ndarray:
     return p
 
 
+@dataclass
+class Rect:
+    cx: float
+    cy: float
+    w: float      # side along angle phi
+    h: float
+    phi: float
+    rho: float    # additive attenuation (1/mm)
+
+
+def rect_line_integrals(geom: Geometry, rects) -> np.ndarray:
+    """Exact line integrals (V, n_b) of rectangles: each ray is mapped into a
+    rectangle's frame and clipped by its two slabs; the chord times the
+    density."""
+    src, u = ray_lines(geom)
+    p = np.zeros((geom.n_views, geom.n_bins))
+    for r in rects:
+        c, s = math.cos(r.phi), math.sin(r.phi)
+        sx, sy = src[..., 0] - r.cx, src[..., 1] - r.cy
+        px, py = sx * c + sy * s, -sx * s + sy * c          # source in the rectangle's frame
+        ux, uy = u[..., 0] * c + u[..., 1] * s, -u[..., 0] * s + u[..., 1] * c
+        lo = np.full(px.shape, -np.inf)
+        hi = np.full(px.shape, np.inf)
+        for q, d, half in ((px, ux, 0.5 * r.w), (py, uy, 0.5 * r.h)):
+            with np.errstate(divide="ignore", invalid="ignore"):
+                t1, t2 = (-half - q) / d, (half - q) / d
+            par = d == 0.0
+            inside = np.abs(q) < half
+            t_lo = np.where(par, np.where(inside, -np.inf, np.inf), np.minimum(t1, t2))
+            t_hi = np.where(par, np.where(inside, np.inf, -np.inf), np.maximum(t1, t2))
+            lo, hi = np.maximum(lo, t_lo), np.minimum(hi, t_hi)
+        p += r.rho * np.maximum(hi - lo, 0.0)
+    return p
+
+
+def shape_line_integrals(geom: Geometry, shapes) -> np.ndarray:
+    """Line integrals of a list of Ellipse and Rect shapes."""
+    ell = [e for e in shapes if isinstance(e, Ellipse)]
+    rec = [r for r in shapes if isinstance(r, Rect)]
+    return ellipse_line_integrals(geom, ell) + rect_line_integrals(geom, rec)
+
+
+# ---------------------------------------------------- evaluation phantoms ----
+# Synthetic stand-ins for the paper's image-quality phantom (resolution and
+# contrast slices, Figs. 1-4): a water-like disk with bar groups, and one with
+# four low-contrast disk targets.
+PHANTOM_RADIUS = 150.0   # mm
+BAR_LP_CM = (2.0, 3.0, 4.0, 5.0)
+
+
+def resolution_phantom(n_bars: int = 5, bar_len: float = 20.0, contrast: float = 0.5 * MU_MAX):
+    """Disk of MU_MAX with, per frequency in BAR_LP_CM, a group of n_bars bars
+    of width 10/(2 lp) mm and period 10/lp mm (vertical bars: the profile runs
+    along x), the groups on a ring of 60 mm.  Returns (shapes, groups) with
+    groups[lp] = (centre x, centre y, bar width)."""
+    shapes = [Ellipse(0.0, 0.0, PHANTOM_RADIUS, PHANTOM_RADIUS, 0.0, MU_MAX)]
+    groups = {}
+    for k, lp in enumerate(BAR_LP_CM):
+        width = 10.0 / (2.0 * lp)
+        ang = 2.0 * math.pi * k / len(BAR_LP_CM) + math.pi / 4
+        gx, gy = 60.0 * math.cos(ang), 60.0 * math.sin(ang)
+        for b in range(n_bars):
+            x = gx + (b - (n_bars - 1) / 2) * 2.0 * width
+            shapes.append(Rect(x, gy, width, bar_len, 0.0, contrast))
+        groups[lp] = (gx, gy, width)
+    return shapes, groups
+
+
+CONTRAST_TARGETS = ((12.0, 0.10), (10.0, 0.05), (8.0, 0.03), (6.0, 0.02))   # (radius mm, relative contrast)
+
+
+def contrast_phantom():
+    """Disk of MU_MAX with four disk targets (ROI 1-4) of decreasing size and
+    relative contrast on a ring of 70 mm.  Returns (shapes, rois) with
+    rois[i] = (centre x, centre y, radius)."""
+    shapes = [Ellipse(0.0, 0.0, PHANTOM_RADIUS, PHANTOM_RADIUS, 0.0, MU_MAX)]
+    rois = []
+    for k, (r, c) in enumerate(CONTRAST_TARGETS):
+        ang = 2.0 * math.pi * k / len(CONTRAST_TARGETS)
+        x, y = 70.0 * math.cos(ang), 70.0 * math.sin(ang)
+        shapes.append(Ellipse(x, y, r, r, 0.0, c * MU_MAX))
+        rois.append((x, y, r))
+    return shapes, rois
+
+
 def noisy_sinogram(p: np.ndarray, photons: float, seed: int) -> np.ndarray:
     """Y = -ln(max(counts, 1)/I0), counts ~ Poisson(I0 exp(-p))."""
     rng = np.random.Generator(np.random.PCG64(seed + 0x5EED))
@@ -214,7 +299,10 @@ def rasterize(geom: Geometry, ellipses, ss: int = 4) -> np.ndarray:
         c, s = math.cos(e.phi), math.sin(e.phi)
         u = (xx - e.cx) * c + (yy - e.cy) * s
         v = -(xx - e.cx) * s + (yy - e.cy) * c
-        X += e.rho * ((u / e.a) ** 2 + (v / e.b) ** 2 <= 1.0)
+        if isinstance(e, Rect):
+            X += e.rho * ((np.abs(u) <= 0.5 * e.w) & (np.abs(v) <= 0.5 * e.h))
+        else:
+            X += e.rho * ((u / e.a) ** 2 + (v / e.b) ** 2 <= 1.0)
     return X.reshape(n, ss, n, ss).mean(axis=(1, 3))
 
 
