@@ -134,13 +134,14 @@ __device__ __forceinline__ bool reduce_tiles(const SliceDesc &s, int tile, int n
 // strip, with the same integer overlaps the projector computes, and the lane
 // adds ov * (c z) to its own shared-memory accumulator of that pixel.
 // Accumulators are laid out [row][lane], so the 32 lanes of a warp always hit
-// 32 different banks, and have one padding row on each side that catches
-// spans just outside the tile (discarded).  Each pixel's sum is formed in a
+// 32 different banks, and have one margin row on each side that catches
+// spans just outside the tile, plus two spill rows that take every lane whose
+// span misses the strip (all discarded): the update runs without a branch.  Each pixel's sum is formed in a
 // fixed order by one lane per half-warp; the halves are summed in a fixed
 // order, and the S parts by OP_BWD_FIN.
 // ======================================================================
 constexpr int BWD_WARPS = AIR_THREADS / 32;
-constexpr int BWD_ROWS = BWD_T + 2;                 // rows -1 .. 16 of a strip
+constexpr int BWD_ROWS = BWD_T + 4;                 // rows -1 .. 16 of a strip, then two spill rows
 constexpr int BWD_ORI = BWD_ROWS * 32;              // one orientation of one warp: [row][lane]
 constexpr int BWD_CHUNK = 32;                       // rays a warp stages at a time
 // per warp: accumulators [orientation][row][lane], then the staged rays as
@@ -153,19 +154,21 @@ constexpr int BWD_SMEM_FLOATS = BWD_WARPS * BWD_WARP_FLOATS;
 // (the tile's column or row) finds its span at lo = L0' + k M, formed as
 // the 32 x 32 -> 64-bit product k * Mlo plus L0', with k * (high word of M)
 // added to the top: the top word is then the pixel row i0 + 1 in the strip.
-__device__ __forceinline__ void bwd_ray(const float4 A, const float4 B, unsigned k, float *a) {
+__device__ __forceinline__ void bwd_ray(const float4 A, const float2 B, unsigned k, float *a) {
     const unsigned long long L0 = ((unsigned long long)__float_as_uint(A.y) << 32) | __float_as_uint(A.x);
     const unsigned long long p = (unsigned long long)k * __float_as_uint(A.z) + L0;
-    const int row = (int)(unsigned)(p >> 32) + (int)k * __float_as_int(B.y);
+    const unsigned row = (unsigned)(p >> 32) + k * (unsigned)__float_as_int(B.y);
     const unsigned Ma = __float_as_uint(A.w);
     const unsigned t = (unsigned)p + Ma;
     const unsigned ov1 = t < Ma ? t : 0u;          // t < Ma iff the add wrapped: the span enters row i0 + 1
     const unsigned ov0 = Ma - ov1;
-    if ((unsigned)row < (unsigned)(BWD_T + 1)) {   // i0 in [-1, 15]
-        float *ap = a + row * 32;
-        ap[0] = fmaf(__uint2float_rn(ov0), B.x, ap[0]);
-        if (ov1 != 0u) ap[32] = fmaf(__uint2float_rn(ov1), B.x, ap[32]);
-    }
+    // strip rows 0 .. BWD_T + 1 are pixel rows -1 .. 16; a span starting
+    // anywhere else lands in the spill rows BWD_T + 2 and BWD_T + 3.  Without
+    // a wrap ov1 = 0 and the second update adds an exact zero.
+    float *ap = a + min(row, (unsigned)(BWD_T + 2)) * 32;
+    const float a0 = ap[0], a1 = ap[32];
+    ap[0] = fmaf(__uint2float_rn(ov0), B.x, a0);
+    ap[32] = fmaf(__uint2float_rn(ov1), B.x, a1);
 }
 
 __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile, float *sm) {
@@ -234,13 +237,14 @@ __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile,
                 const unsigned k = colv ? kH : kV;
                 float *a = colv ? aH : aV;
 #pragma unroll 2
-                for (int i = h; i < cnt; i += 2) bwd_ray(stA[i], stB[i], k, a);
+                for (int i = h; i < cnt; i += 2)
+                    bwd_ray(stA[i], *reinterpret_cast<const float2 *>(stB + i), k, a);
             } else {
 #pragma unroll 1
                 for (int i = h; i < cnt; i += 2) {
                     const float4 B = stB[i];
                     const bool col = __float_as_int(B.z) != 0;
-                    bwd_ray(stA[i], B, col ? kH : kV, col ? aH : aV);
+                    bwd_ray(stA[i], make_float2(B.x, B.y), col ? kH : kV, col ? aH : aV);
                 }
             }
             __syncwarp();
