@@ -87,10 +87,13 @@ __host__ __device__ inline long long ray_M(const RayFx &r) {
 }
 
 // Per (view, backprojector pixel tile): the rays of the view that can meet
-// the tile, [J0, J1), and whether they all walk the same way.
-constexpr unsigned VT_MIXED = 1u << 29;   // the range holds both orientations
-__host__ __device__ inline unsigned vt_pack(int j0, int j1, int o, bool mixed) {
-    return (unsigned)j0 | ((unsigned)j1 << 14) | ((unsigned)o << 28) | (mixed ? VT_MIXED : 0u);
+// the tile, [J0, J1), the orientation and slope sign of ray J0, and whether
+// all rays of the range share both.
+constexpr unsigned VT_MIXED = 1u << 29;   // the range holds both orientations or both signs of M
+constexpr unsigned VT_NEG = 1u << 30;     // ray J0 has M < 0
+__host__ __device__ inline unsigned vt_pack(int j0, int j1, int o, bool neg, bool mixed) {
+    return (unsigned)j0 | ((unsigned)j1 << 14) | ((unsigned)o << 28) | (neg ? VT_NEG : 0u) |
+           (mixed ? VT_MIXED : 0u);
 }
 
 // Everything a tile function needs to know about one slice.  Plain data:

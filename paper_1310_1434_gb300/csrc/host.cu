@@ -336,14 +336,14 @@ air_status build_tables(const air_geometry &g, double dg, int ntxy, HostTables &
     // whose fan angle lies between the extreme fan angles of the tile's
     // corners (the tile is convex and the source outside it, so exactly
     // these rays can meet it), widened by 0.02 bin; and whether they all walk
-    // the same way.  Fan angles at the corner grid are shared by neighbouring
-    // tiles.
+    // the same way with slopes of one sign.  Fan angles at the corner grid
+    // are shared by neighbouring tiles.
     const int tpr = (n + BWD_T - 1) / BWD_T;
     std::vector<unsigned> &hvt = T.vt;
     hvt.assign((size_t)V * ntxy, 0u);
     {
         std::vector<double> gam((size_t)(tpr + 1) * (tpr + 1));
-        std::vector<int> chg(nb);   // number of orientation changes among rays 0..j
+        std::vector<int> chg(nb);   // number of changes of orientation or slope sign among rays 0..j
         const double jm = 0.5 * (nb - 1);
         for (int v = 0; v < V; ++v) {
             const double4 w = hsrc[v];
@@ -355,7 +355,8 @@ air_status build_tables(const air_geometry &g, double dg, int ntxy, HostTables &
                 }
             const RayFx *rv = hray.data() + (size_t)v * nb;
             chg[0] = 0;
-            for (int j = 1; j < nb; ++j) chg[j] = chg[j - 1] + (rv[j].o != rv[j - 1].o);
+            for (int j = 1; j < nb; ++j)
+                chg[j] = chg[j - 1] + (rv[j].o != rv[j - 1].o || (rv[j].cs < 0.f) != (rv[j - 1].cs < 0.f));
             for (int ty = 0; ty < tpr; ++ty)
                 for (int tx = 0; tx < tpr; ++tx) {
                     double gmin = 1e30, gmax = -1e30;
@@ -368,8 +369,8 @@ air_status build_tables(const air_geometry &g, double dg, int ntxy, HostTables &
                     const double f0 = std::ceil(gmin / dg + jm - 0.02), f1 = std::floor(gmax / dg + jm + 0.02);
                     const int j0 = (int)std::max(0.0, std::min(f0, (double)nb));
                     const int j1 = (int)std::max(-1.0, std::min(f1, (double)nb - 1));   // inclusive
-                    unsigned ent = vt_pack(0, 0, 0, false);
-                    if (j1 >= j0) ent = vt_pack(j0, j1 + 1, rv[j0].o, chg[j1] != chg[j0]);
+                    unsigned ent = vt_pack(0, 0, 0, false, false);
+                    if (j1 >= j0) ent = vt_pack(j0, j1 + 1, rv[j0].o, rv[j0].cs < 0.f, chg[j1] != chg[j0]);
                     hvt[(size_t)(ty * tpr + tx) * V + v] = ent;
                 }
         }

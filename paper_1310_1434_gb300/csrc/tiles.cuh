@@ -144,21 +144,24 @@ constexpr int BWD_WARPS = AIR_THREADS / 32;
 constexpr int BWD_ROWS = BWD_T + 4;                 // rows -1 .. 16 of a strip, then two spill rows
 constexpr int BWD_ORI = BWD_ROWS * 32;              // one orientation of one warp: [row][lane]
 constexpr int BWD_CHUNK = 32;                       // rays a warp stages at a time
-// per warp: accumulators [orientation][row][lane], then the staged rays as
-// two float4 per ray
-constexpr int BWD_WARP_FLOATS = 2 * BWD_ORI + 2 * 4 * BWD_CHUNK;
+// per warp: accumulators [orientation][row][lane], then the staged rays (one
+// float4 each) and their orientation / sign flags
+constexpr int BWD_WARP_FLOATS = 2 * BWD_ORI + 4 * BWD_CHUNK + BWD_CHUNK;
 constexpr int BWD_SMEM_FLOATS = BWD_WARPS * BWD_WARP_FLOATS;
 
-// A staged ray, relative to the tile: {L0 - (base - 1) 2^32 as two words,
-// Mlo, |M|} and {c z, high word of M, orientation}.  Lane k of the walk
-// (the tile's column or row) finds its span at lo = L0' + k M, formed as
-// the 32 x 32 -> 64-bit product k * Mlo plus L0', with k * (high word of M)
-// added to the top: the top word is then the pixel row i0 + 1 in the strip.
-__device__ __forceinline__ void bwd_ray(const float4 A, const float2 B, unsigned k, float *a) {
-    const unsigned long long L0 = ((unsigned long long)__float_as_uint(A.y) << 32) | __float_as_uint(A.x);
-    const unsigned long long p = (unsigned long long)k * __float_as_uint(A.z) + L0;
-    const unsigned row = (unsigned)(p >> 32) + k * (unsigned)__float_as_int(B.y);
-    const unsigned Ma = __float_as_uint(A.w);
+// A staged ray, relative to the tile and to the lane's walk index:
+// {low and high word of L0'', |M|, c z}.  Lane c of a half-warp takes the
+// tile's column (row) X0 + c; with kb = X0 for M > 0 and kb = X0 + 15 for
+// M < 0, and the walk index kk = c or 15 - c to match, the span of that
+// column starts at lo = L0 + (X0 + c) M = L0 + kb M + kk |M|.  Staging folds
+// L0 + kb M, shifted by the strip's first row (base - 1) 2^32, into L0'', so
+// that the lane forms lo as one 32 x 32 -> 64-bit product plus L0'' (the same
+// 64-bit value the projector walks to) and its top word is the strip row.
+__device__ __forceinline__ void bwd_ray(const float4 A, unsigned kk, float *a) {
+    const unsigned long long L = ((unsigned long long)__float_as_uint(A.y) << 32) | __float_as_uint(A.x);
+    const unsigned Ma = __float_as_uint(A.z);
+    const unsigned long long p = (unsigned long long)kk * Ma + L;
+    const unsigned row = (unsigned)(p >> 32);
     const unsigned t = (unsigned)p + Ma;
     const unsigned ov1 = t < Ma ? t : 0u;          // t < Ma iff the add wrapped: the span enters row i0 + 1
     const unsigned ov0 = Ma - ov1;
@@ -167,8 +170,8 @@ __device__ __forceinline__ void bwd_ray(const float4 A, const float2 B, unsigned
     // a wrap ov1 = 0 and the second update adds an exact zero.
     float *ap = a + min(row, (unsigned)(BWD_T + 2)) * 32;
     const float a0 = ap[0], a1 = ap[32];
-    ap[0] = fmaf(__uint2float_rn(ov0), B.x, a0);
-    ap[32] = fmaf(__uint2float_rn(ov1), B.x, a1);
+    ap[0] = fmaf(__uint2float_rn(ov0), A.w, a0);
+    ap[32] = fmaf(__uint2float_rn(ov1), A.w, a1);
 }
 
 __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile, float *sm) {
@@ -187,8 +190,7 @@ __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile,
     float *aH = wsm + lane;                         // rays walking columns: [row][lane = column]
     float *aV = aH + BWD_ORI;                       // rays walking rows:    [column][lane = row]
     float4 *stA = reinterpret_cast<float4 *>(wsm + 2 * BWD_ORI);
-    float4 *stB = stA + BWD_CHUNK;
-    const unsigned kH = X0 + c, kV = Y0 + c;
+    int *stF = reinterpret_cast<int *>(stA + BWD_CHUNK);        // bit 0: walks columns, bit 1: M < 0
     const int S = s.bwd_parts, dv = S * BWD_WARPS;
     const unsigned *__restrict__ vtt = s.vt + (size_t)txy * V;     // this tile's entries, by view
 
@@ -218,33 +220,33 @@ __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile,
 #pragma unroll 1
         for (int c0 = j0; c0 < j1; c0 += BWD_CHUNK) {
             if (c0 != j0) fetch(e, v, c0 + lane);                       // ranges longer than a chunk
-            {   // stage this lane's ray, tile-relative
+            {   // stage this lane's ray, tile- and walk-index-relative (see bwd_ray)
                 const bool col = mixed ? ro != 0 : colv;
-                const long long basem1 = (long long)((col ? Y0 : X0) - 1);
-                const unsigned long long L0 =
-                    (((unsigned long long)__float_as_uint(rq.y) << 32) | __float_as_uint(rq.x)) -
-                    ((unsigned long long)basem1 << 32);
                 const unsigned Mlo = __float_as_uint(rq.z);
-                const int Mhi = __float_as_int(rq.w) >> 31;
-                stA[lane] = make_float4(__uint_as_float((unsigned)L0), __uint_as_float((unsigned)(L0 >> 32)),
-                                        rq.z, __uint_as_float((Mlo ^ (unsigned)Mhi) - (unsigned)Mhi));
-                stB[lane] = make_float4(fabsf(rq.w) * rz, __int_as_float(Mhi), __int_as_float((int)col), 0.f);
+                const bool neg = __float_as_int(rq.w) < 0;          // the sign of c is the sign of M
+                const unsigned kb = (unsigned)(col ? X0 : Y0) + (neg ? BWD_T - 1u : 0u);
+                const unsigned hsub = (unsigned)((col ? Y0 : X0) - 1) + (neg ? kb : 0u);
+                const unsigned long long L =
+                    (unsigned long long)kb * Mlo +
+                    (((unsigned long long)__float_as_uint(rq.y) << 32) | __float_as_uint(rq.x)) -
+                    ((unsigned long long)hsub << 32);
+                stA[lane] = make_float4(__uint_as_float((unsigned)L), __uint_as_float((unsigned)(L >> 32)),
+                                        __uint_as_float(neg ? 0u - Mlo : Mlo), fabsf(rq.w) * rz);
+                stF[lane] = (int)col | (neg ? 2 : 0);
             }
             __syncwarp();
             const int cnt = min(BWD_CHUNK, j1 - c0);
             if (c0 + BWD_CHUNK >= j1 && vn < V) fetch(en, vn, (int)(en & 0x3fffu) + lane);   // next view
             if (!mixed) {
-                const unsigned k = colv ? kH : kV;
+                const unsigned kk = (e & VT_NEG) ? BWD_T - 1u - c : (unsigned)c;
                 float *a = colv ? aH : aV;
 #pragma unroll 2
-                for (int i = h; i < cnt; i += 2)
-                    bwd_ray(stA[i], *reinterpret_cast<const float2 *>(stB + i), k, a);
+                for (int i = h; i < cnt; i += 2) bwd_ray(stA[i], kk, a);
             } else {
 #pragma unroll 1
                 for (int i = h; i < cnt; i += 2) {
-                    const float4 B = stB[i];
-                    const bool col = __float_as_int(B.z) != 0;
-                    bwd_ray(stA[i], make_float2(B.x, B.y), col ? kH : kV, col ? aH : aV);
+                    const int f = stF[i];
+                    bwd_ray(stA[i], (f & 2) ? BWD_T - 1u - c : (unsigned)c, (f & 1) ? aH : aV);
                 }
             }
             __syncwarp();
