@@ -136,17 +136,22 @@ __device__ __forceinline__ bool reduce_tiles(const SliceDesc &s, int tile, int n
 // Accumulators are laid out [row][lane], so the 32 lanes of a warp always hit
 // 32 different banks, and have one margin row on each side that catches
 // spans just outside the tile, plus two spill rows that take every lane whose
-// span misses the strip (all discarded): the update runs without a branch.  Each pixel's sum is formed in a
+// span misses the strip (all discarded): the update runs without a branch.
+// The two orientations share the spill rows: rays walking columns count their
+// strip rows up from the start of the warp's area, rays walking rows count
+// theirs down from its end.  Each pixel's sum is formed in a
 // fixed order by one lane per half-warp; the halves are summed in a fixed
 // order, and the S parts by OP_BWD_FIN.
 // ======================================================================
 constexpr int BWD_WARPS = AIR_THREADS / 32;
-constexpr int BWD_ROWS = BWD_T + 4;                 // rows -1 .. 16 of a strip, then two spill rows
-constexpr int BWD_ORI = BWD_ROWS * 32;              // one orientation of one warp: [row][lane]
+constexpr int BWD_ROWS = BWD_T + 2;                 // rows -1 .. 16 of a strip
+constexpr int BWD_SPILL = BWD_T + 2;                // first spill row (a start row clamps to it)
+constexpr int BWD_ACC = (2 * BWD_ROWS + 2) * 32;    // one warp's accumulators: [row][lane]
 constexpr int BWD_CHUNK = 32;                       // rays a warp stages at a time
-// per warp: accumulators [orientation][row][lane], then the staged rays (one
-// float4 each) and their orientation / sign flags
-constexpr int BWD_WARP_FLOATS = 2 * BWD_ORI + 4 * BWD_CHUNK + BWD_CHUNK;
+// per warp: accumulators (columns-walking strip rows 0..17, spill rows 18
+// and 19, rows-walking strip rows 17..0), then the staged rays (one float4
+// each) and their orientation / sign flags
+constexpr int BWD_WARP_FLOATS = BWD_ACC + 4 * BWD_CHUNK + BWD_CHUNK;
 constexpr int BWD_SMEM_FLOATS = BWD_WARPS * BWD_WARP_FLOATS;
 
 // A staged ray, relative to the tile and to the lane's walk index:
@@ -157,6 +162,7 @@ constexpr int BWD_SMEM_FLOATS = BWD_WARPS * BWD_WARP_FLOATS;
 // L0 + kb M, shifted by the strip's first row (base - 1) 2^32, into L0'', so
 // that the lane forms lo as one 32 x 32 -> 64-bit product plus L0'' (the same
 // 64-bit value the projector walks to) and its top word is the strip row.
+template <int STRIDE>   // +32: rays walking columns, -32: rays walking rows
 __device__ __forceinline__ void bwd_ray(const float4 A, unsigned kk, float *a) {
     const unsigned long long L = ((unsigned long long)__float_as_uint(A.y) << 32) | __float_as_uint(A.x);
     const unsigned Ma = __float_as_uint(A.z);
@@ -166,12 +172,12 @@ __device__ __forceinline__ void bwd_ray(const float4 A, unsigned kk, float *a) {
     const unsigned ov1 = t < Ma ? t : 0u;          // t < Ma iff the add wrapped: the span enters row i0 + 1
     const unsigned ov0 = Ma - ov1;
     // strip rows 0 .. BWD_T + 1 are pixel rows -1 .. 16; a span starting
-    // anywhere else lands in the spill rows BWD_T + 2 and BWD_T + 3.  Without
-    // a wrap ov1 = 0 and the second update adds an exact zero.
-    float *ap = a + min(row, (unsigned)(BWD_T + 2)) * 32;
-    const float a0 = ap[0], a1 = ap[32];
+    // anywhere else lands in the spill rows BWD_SPILL and BWD_SPILL + 1.
+    // Without a wrap ov1 = 0 and the second update adds an exact zero.
+    float *ap = a + (int)min(row, (unsigned)BWD_SPILL) * STRIDE;
+    const float a0 = ap[0], a1 = ap[STRIDE];
     ap[0] = fmaf(__uint2float_rn(ov0), A.w, a0);
-    ap[32] = fmaf(__uint2float_rn(ov1), A.w, a1);
+    ap[STRIDE] = fmaf(__uint2float_rn(ov1), A.w, a1);
 }
 
 __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile, float *sm) {
@@ -186,10 +192,11 @@ __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile,
     const int h = lane >> 4, c = lane & 15;
     const float *__restrict__ Z = mode == BWD_PLAIN ? s.ext_in : s.zc;
     float *wsm = sm + warp * BWD_WARP_FLOATS;
-    // this lane's accumulator column: row i of orientation o at aH/aV + (i + 1) * 32
+    // this lane's accumulator column: strip row r (pixel row or column r - 1)
+    // at aH + 32 r for rays walking columns, aV - 32 r for rays walking rows
     float *aH = wsm + lane;                         // rays walking columns: [row][lane = column]
-    float *aV = aH + BWD_ORI;                       // rays walking rows:    [column][lane = row]
-    float4 *stA = reinterpret_cast<float4 *>(wsm + 2 * BWD_ORI);
+    float *aV = aH + (2 * BWD_ROWS + 1) * 32;       // rays walking rows:    [column][lane = row], reversed
+    float4 *stA = reinterpret_cast<float4 *>(wsm + BWD_ACC);
     int *stF = reinterpret_cast<int *>(stA + BWD_CHUNK);        // bit 0: walks columns, bit 1: M < 0
     const int S = s.bwd_parts, dv = S * BWD_WARPS;
     const unsigned *__restrict__ vtt = s.vt + (size_t)txy * V;     // this tile's entries, by view
@@ -239,14 +246,20 @@ __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile,
             if (c0 + BWD_CHUNK >= j1 && vn < V) fetch(en, vn, (int)(en & 0x3fffu) + lane);   // next view
             if (!mixed) {
                 const unsigned kk = (e & VT_NEG) ? BWD_T - 1u - c : (unsigned)c;
-                float *a = colv ? aH : aV;
+                if (colv) {
 #pragma unroll 2
-                for (int i = h; i < cnt; i += 2) bwd_ray(stA[i], kk, a);
+                    for (int i = h; i < cnt; i += 2) bwd_ray<32>(stA[i], kk, aH);
+                } else {
+#pragma unroll 2
+                    for (int i = h; i < cnt; i += 2) bwd_ray<-32>(stA[i], kk, aV);
+                }
             } else {
 #pragma unroll 1
                 for (int i = h; i < cnt; i += 2) {
                     const int f = stF[i];
-                    bwd_ray(stA[i], (f & 2) ? BWD_T - 1u - c : (unsigned)c, (f & 1) ? aH : aV);
+                    const unsigned kk = (f & 2) ? BWD_T - 1u - c : (unsigned)c;
+                    if (f & 1) bwd_ray<32>(stA[i], kk, aH);
+                    else bwd_ray<-32>(stA[i], kk, aV);
                 }
             }
             __syncwarp();
@@ -260,7 +273,7 @@ __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile,
 #pragma unroll 4
     for (int k = 0; k < BWD_WARPS * 2; ++k) {    // (warp, half) in a fixed order
         const float *b = sm + (k >> 1) * BWD_WARP_FLOATS + (k & 1) * 16;
-        acc += b[(ly + 1) * 32 + lx] + b[BWD_ORI + (lx + 1) * 32 + ly];
+        acc += b[(ly + 1) * 32 + lx] + b[(2 * BWD_ROWS + 1 - (lx + 1)) * 32 + ly];
     }
     const int ix = X0 + lx, iy = Y0 + ly;
     if (ix < n && iy < n) {
