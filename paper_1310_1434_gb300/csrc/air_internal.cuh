@@ -155,8 +155,8 @@ __host__ __device__ inline int tiles_fwd(const SliceDesc &s) {
     return ((s.V + s.fwd_vpb - 1) / s.fwd_vpb) * ((s.nb + bpb - 1) / bpb);
 }
 __host__ __device__ inline int tiles_ramp(const SliceDesc &s) { return s.V; }
-// backprojector tile: 16 x 16 pixels x one of bwd_parts view parts
-constexpr int BWD_T = 16;
+// backprojector tile: 32 x 32 pixels x one of bwd_parts view parts
+constexpr int BWD_T = 32;
 __host__ __device__ inline int tiles_bwd_xy(const SliceDesc &s) {
     return ((s.n + BWD_T - 1) / BWD_T) * ((s.n + BWD_T - 1) / BWD_T);
 }

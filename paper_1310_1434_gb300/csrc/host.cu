@@ -99,9 +99,10 @@ size_t plan_bytes_estimate(const air_geometry &g) {
     s.V = g.n_views;
     s.nb = g.n_bins;
     const size_t nn = (size_t)g.n * g.n, rays = (size_t)g.n_views * g.n_bins;
-    const size_t parts = (size_t)choose_bwd_parts(s);
+    // the part buffer holds the autotuner's largest split, as plan_build sizes it
+    const size_t parts = (size_t)std::min(g.n_views, 2 * choose_bwd_parts(s));
     size_t b = rays * sizeof(RayFx) + (size_t)g.n_views * tiles_bwd_xy(s) * 4 + (size_t)g.n_bins * 4;
-    b += nn * 4 * (7 + 2 * parts + 18 + 1);      // x r p q rhs0 g g', parts (up to 2x), b b2, xbuf
+    b += nn * 4 * (7 + parts + 18 + 1);          // x r p q rhs0 g g', parts, b b2, xbuf
     b += (size_t)g.n * (g.n + 2) * 4 * 2;        // xp xt
     b += (size_t)g.n_views * 8 + (size_t)g.n_bins * 8;   // FBP tables
     b += rays * 4 * 3;                           // z zc ybuf
@@ -332,7 +333,7 @@ air_status build_tables(const air_geometry &g, double dg, int ntxy, HostTables &
         }
         if (!ok) return fail(AIR_ERR_INTERNAL, "ray table: a walk range leaves the image");
     }
-    // backprojector ray ranges: per view and 16 x 16 pixel tile, the rays
+    // backprojector ray ranges: per view and 32 x 32 pixel tile, the rays
     // whose fan angle lies between the extreme fan angles of the tile's
     // corners (the tile is convex and the source outside it, so exactly
     // these rays can meet it), widened by 0.02 bin; and whether they all walk

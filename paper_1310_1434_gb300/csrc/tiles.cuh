@@ -125,44 +125,43 @@ __device__ __forceinline__ bool reduce_tiles(const SliceDesc &s, int tile, int n
 
 // ======================================================================
 // Backprojector A^T, the exact transpose of tile_fwd, without atomics.
-// A tile is a 16 x 16 block of pixels and one of S parts of the views.  Each
-// warp takes whole views; for each it sweeps the rays of the view that meet
-// the tile (a range the plan computes, see vt_pack), two rays at a time: half
-// h of the warp takes rays J0 + h, J0 + h + 2, ...  Lane c of a half takes
-// the tile's column c for rays that walk columns and its row c for rays that
-// walk rows; there the ray's span touches one or two pixels of the lane's
-// strip, with the same integer overlaps the projector computes, and the lane
-// adds ov * (c z) to its own shared-memory accumulator of that pixel.
-// Accumulators are laid out [row][lane], so the 32 lanes of a warp always hit
-// 32 different banks, and have one margin row on each side that catches
-// spans just outside the tile, plus two spill rows that take every lane whose
-// span misses the strip (all discarded): the update runs without a branch.
-// The two orientations share the spill rows: rays walking columns count their
-// strip rows up from the start of the warp's area, rays walking rows count
-// theirs down from its end.  Each pixel's sum is formed in a
-// fixed order by one lane per half-warp; the halves are summed in a fixed
-// order, and the S parts by OP_BWD_FIN.
+// A tile is a 32 x 32 block of pixels and one of S parts of the views.  Warps
+// 0-3 take the rays that walk columns, warps 4-7 the rays that walk rows, of
+// the same views (warp w: views part + S (w mod 4) + 4 S k).  For each view a
+// warp sweeps the rays of the view that meet the tile (a range the plan
+// computes, see vt_pack) one ray per step: lane c takes the tile's column c
+// (row c for rays walking rows); there the ray's span touches one or two
+// pixels of the lane's strip, with the same integer overlaps the projector
+// computes, and the lane adds ov * (c z) to its own shared-memory
+// accumulator of that pixel.  Accumulators are laid out [strip row][lane], so
+// the 32 lanes of a warp always hit 32 different banks, with one margin row
+// on each side that catches spans just outside the tile and two spill rows
+// that take every lane whose span misses the strip (all discarded): the
+// update runs without a branch.  Each pixel's sum is formed in a fixed order
+// by one lane of each warp; the warps are summed in a fixed order, and the S
+// parts by OP_BWD_FIN.
 // ======================================================================
+static_assert(BWD_T == 32, "lane c of a warp owns column (row) c of a backprojector tile");
 constexpr int BWD_WARPS = AIR_THREADS / 32;
-constexpr int BWD_ROWS = BWD_T + 2;                 // rows -1 .. 16 of a strip
-constexpr int BWD_SPILL = BWD_T + 2;                // first spill row (a start row clamps to it)
-constexpr int BWD_ACC = (2 * BWD_ROWS + 2) * 32;    // one warp's accumulators: [row][lane]
+constexpr int BWD_GROUP = BWD_WARPS / 2;            // warps per orientation
+constexpr int BWD_ROWS = BWD_T + 2;                 // strip rows: pixel rows -1 .. 32
+constexpr int BWD_SPILL = BWD_ROWS;                 // first spill row (a start row clamps to it)
+constexpr int BWD_ACC = (BWD_ROWS + 2) * 32;        // one warp's accumulators: [row][lane]
 constexpr int BWD_CHUNK = 32;                       // rays a warp stages at a time
-// per warp: accumulators (columns-walking strip rows 0..17, spill rows 18
-// and 19, rows-walking strip rows 17..0), then the staged rays (one float4
-// each) and their orientation / sign flags
+// per warp: accumulators, then the staged rays (one float4 each) and their
+// orientation / sign flags
 constexpr int BWD_WARP_FLOATS = BWD_ACC + 4 * BWD_CHUNK + BWD_CHUNK;
 constexpr int BWD_SMEM_FLOATS = BWD_WARPS * BWD_WARP_FLOATS;
+static_assert(BWD_ACC >= BWD_T * (BWD_T + 1), "the final sum's staging fits in one warp's accumulators");
 
 // A staged ray, relative to the tile and to the lane's walk index:
-// {low and high word of L0'', |M|, c z}.  Lane c of a half-warp takes the
-// tile's column (row) X0 + c; with kb = X0 for M > 0 and kb = X0 + 15 for
-// M < 0, and the walk index kk = c or 15 - c to match, the span of that
-// column starts at lo = L0 + (X0 + c) M = L0 + kb M + kk |M|.  Staging folds
-// L0 + kb M, shifted by the strip's first row (base - 1) 2^32, into L0'', so
-// that the lane forms lo as one 32 x 32 -> 64-bit product plus L0'' (the same
-// 64-bit value the projector walks to) and its top word is the strip row.
-template <int STRIDE>   // +32: rays walking columns, -32: rays walking rows
+// {low and high word of L0'', |M|, c z}.  Lane c takes the tile's column
+// (row) X0 + c; with kb = X0 for M > 0 and kb = X0 + 31 for M < 0, and the
+// walk index kk = c or 31 - c to match, the span of that column starts at
+// lo = L0 + (X0 + c) M = L0 + kb M + kk |M|.  Staging folds L0 + kb M,
+// shifted by the strip's first row (base - 1) 2^32, into L0'', so that the
+// lane forms lo as one 32 x 32 -> 64-bit product plus L0'' (the same 64-bit
+// value the projector walks to) and its top word is the strip row.
 __device__ __forceinline__ void bwd_ray(const float4 A, unsigned kk, float *a) {
     const unsigned long long L = ((unsigned long long)__float_as_uint(A.y) << 32) | __float_as_uint(A.x);
     const unsigned Ma = __float_as_uint(A.z);
@@ -171,13 +170,13 @@ __device__ __forceinline__ void bwd_ray(const float4 A, unsigned kk, float *a) {
     const unsigned t = (unsigned)p + Ma;
     const unsigned ov1 = t < Ma ? t : 0u;          // t < Ma iff the add wrapped: the span enters row i0 + 1
     const unsigned ov0 = Ma - ov1;
-    // strip rows 0 .. BWD_T + 1 are pixel rows -1 .. 16; a span starting
+    // strip rows 0 .. BWD_T + 1 are pixel rows -1 .. 32; a span starting
     // anywhere else lands in the spill rows BWD_SPILL and BWD_SPILL + 1.
     // Without a wrap ov1 = 0 and the second update adds an exact zero.
-    float *ap = a + (int)min(row, (unsigned)BWD_SPILL) * STRIDE;
-    const float a0 = ap[0], a1 = ap[STRIDE];
+    float *ap = a + min(row, (unsigned)BWD_SPILL) * 32;
+    const float a0 = ap[0], a1 = ap[32];
     ap[0] = fmaf(__uint2float_rn(ov0), A.w, a0);
-    ap[STRIDE] = fmaf(__uint2float_rn(ov1), A.w, a1);
+    ap[32] = fmaf(__uint2float_rn(ov1), A.w, a1);
 }
 
 __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile, float *sm) {
@@ -189,18 +188,20 @@ __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile,
     for (int i = threadIdx.x; i < BWD_SMEM_FLOATS; i += AIR_THREADS) sm[i] = 0.f;
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int h = lane >> 4, c = lane & 15;
+    const bool colw = warp < BWD_GROUP;             // this warp takes the rays that walk columns
+    const unsigned myo = colw ? 1u : 0u;
     const float *__restrict__ Z = mode == BWD_PLAIN ? s.ext_in : s.zc;
     float *wsm = sm + warp * BWD_WARP_FLOATS;
-    // this lane's accumulator column: strip row r (pixel row or column r - 1)
-    // at aH + 32 r for rays walking columns, aV - 32 r for rays walking rows
-    float *aH = wsm + lane;                         // rays walking columns: [row][lane = column]
-    float *aV = aH + (2 * BWD_ROWS + 1) * 32;       // rays walking rows:    [column][lane = row], reversed
+    float *a = wsm + lane;                          // this lane's strip: row r at a + 32 r
     float4 *stA = reinterpret_cast<float4 *>(wsm + BWD_ACC);
     int *stF = reinterpret_cast<int *>(stA + BWD_CHUNK);        // bit 0: walks columns, bit 1: M < 0
-    const int S = s.bwd_parts, dv = S * BWD_WARPS;
+    const int S = s.bwd_parts, dv = S * BWD_GROUP;
     const unsigned *__restrict__ vtt = s.vt + (size_t)txy * V;     // this tile's entries, by view
 
+    // an entry this warp works on: a non-empty range holding rays of its orientation
+    auto mine = [&](unsigned e) {
+        return ((e >> 14) & 0x3fffu) > (e & 0x3fffu) && ((e & VT_MIXED) != 0u || ((e >> 28) & 1u) == myo);
+    };
     // ray j of view v into registers (lane = position in the chunk)
     float4 rq = make_float4(0.f, 0.f, 0.f, 0.f);
     float rz = 0.f;
@@ -213,22 +214,27 @@ __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile,
             if (e & VT_MIXED) ro = rp->o;
         }
     };
-    int v = part + S * warp;
+    int v = part + S * (warp % BWD_GROUP);
     unsigned e = v < V ? __ldg(vtt + v) : 0u;
     unsigned en = v + dv < V ? __ldg(vtt + v + dv) : 0u;
-    if (v < V) fetch(e, v, (int)(e & 0x3fffu) + lane);
+    if (v < V && mine(e)) fetch(e, v, (int)(e & 0x3fffu) + lane);
 #pragma unroll 1
     for (; v < V; v += dv) {
         const int vn = v + dv;
         const unsigned enn = vn + dv < V ? __ldg(vtt + vn + dv) : 0u;   // two views ahead
+        if (!mine(e)) {                                                  // nothing here for this warp
+            if (vn < V && mine(en)) fetch(en, vn, (int)(en & 0x3fffu) + lane);
+            e = en;
+            en = enn;
+            continue;
+        }
         const int j0 = e & 0x3fffu, j1 = (e >> 14) & 0x3fffu;
-        const bool mixed = (e & VT_MIXED) != 0u, colv = ((e >> 28) & 1u) != 0u;
-        if (j0 >= j1 && vn < V) fetch(en, vn, (int)(en & 0x3fffu) + lane);
+        const bool mixed = (e & VT_MIXED) != 0u;
 #pragma unroll 1
         for (int c0 = j0; c0 < j1; c0 += BWD_CHUNK) {
             if (c0 != j0) fetch(e, v, c0 + lane);                       // ranges longer than a chunk
             {   // stage this lane's ray, tile- and walk-index-relative (see bwd_ray)
-                const bool col = mixed ? ro != 0 : colv;
+                const bool col = mixed ? ro != 0 : colw;
                 const unsigned Mlo = __float_as_uint(rq.z);
                 const bool neg = __float_as_int(rq.w) < 0;          // the sign of c is the sign of M
                 const unsigned kb = (unsigned)(col ? X0 : Y0) + (neg ? BWD_T - 1u : 0u);
@@ -243,23 +249,17 @@ __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile,
             }
             __syncwarp();
             const int cnt = min(BWD_CHUNK, j1 - c0);
-            if (c0 + BWD_CHUNK >= j1 && vn < V) fetch(en, vn, (int)(en & 0x3fffu) + lane);   // next view
+            if (c0 + BWD_CHUNK >= j1 && vn < V && mine(en)) fetch(en, vn, (int)(en & 0x3fffu) + lane);   // next view
             if (!mixed) {
-                const unsigned kk = (e & VT_NEG) ? BWD_T - 1u - c : (unsigned)c;
-                if (colv) {
+                const unsigned kk = (e & VT_NEG) ? BWD_T - 1u - lane : (unsigned)lane;
 #pragma unroll 2
-                    for (int i = h; i < cnt; i += 2) bwd_ray<32>(stA[i], kk, aH);
-                } else {
-#pragma unroll 2
-                    for (int i = h; i < cnt; i += 2) bwd_ray<-32>(stA[i], kk, aV);
-                }
+                for (int i = 0; i < cnt; ++i) bwd_ray(stA[i], kk, a);
             } else {
 #pragma unroll 1
-                for (int i = h; i < cnt; i += 2) {
+                for (int i = 0; i < cnt; ++i) {
                     const int f = stF[i];
-                    const unsigned kk = (f & 2) ? BWD_T - 1u - c : (unsigned)c;
-                    if (f & 1) bwd_ray<32>(stA[i], kk, aH);
-                    else bwd_ray<-32>(stA[i], kk, aV);
+                    if ((unsigned)(f & 1) != myo) continue;               // the other orientation's ray
+                    bwd_ray(stA[i], (f & 2) ? BWD_T - 1u - lane : (unsigned)lane, a);
                 }
             }
             __syncwarp();
@@ -268,17 +268,40 @@ __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile,
         en = enn;
     }
     __syncthreads();
-    const int lx = threadIdx.x % BWD_T, ly = threadIdx.x / BWD_T;
-    float acc = 0.f;
-#pragma unroll 4
-    for (int k = 0; k < BWD_WARPS * 2; ++k) {    // (warp, half) in a fixed order
-        const float *b = sm + (k >> 1) * BWD_WARP_FLOATS + (k & 1) * 16;
-        acc += b[(ly + 1) * 32 + lx] + b[(2 * BWD_ROWS + 1 - (lx + 1)) * 32 + ly];
+    // pixel (lx, ly) of the tile: the column-walking warps hold it at strip
+    // row ly + 1, lane lx; the row-walking warps at strip row lx + 1, lane ly.
+    // The row-walking sums are read with lanes along ly (no bank conflicts) and
+    // handed over through a padded [ly][lx] table in warp BWD_GROUP's area.
+    constexpr int PIX = BWD_T * BWD_T / AIR_THREADS;
+    float vs[PIX];
+#pragma unroll
+    for (int q = 0; q < PIX; ++q) {
+        const int p = threadIdx.x + q * AIR_THREADS, ly = p & 31, lx = p >> 5;
+        float acc = 0.f;
+#pragma unroll
+        for (int w = BWD_GROUP; w < BWD_WARPS; ++w) acc += sm[w * BWD_WARP_FLOATS + (lx + 1) * 32 + ly];
+        vs[q] = acc;
     }
-    const int ix = X0 + lx, iy = Y0 + ly;
-    if (ix < n && iy < n) {
-        if (S == 1 && mode == BWD_PLAIN) s.ext_out[iy * n + ix] = s.dx * acc;
-        else s.bwd_part[(size_t)part * n * n + iy * n + ix] = acc;
+    __syncthreads();
+    float *hand = sm + BWD_GROUP * BWD_WARP_FLOATS;
+#pragma unroll
+    for (int q = 0; q < PIX; ++q) {
+        const int p = threadIdx.x + q * AIR_THREADS, ly = p & 31, lx = p >> 5;
+        hand[ly * 33 + lx] = vs[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PIX; ++q) {
+        const int p = threadIdx.x + q * AIR_THREADS, lx = p & 31, ly = p >> 5;
+        float acc = 0.f;
+#pragma unroll
+        for (int w = 0; w < BWD_GROUP; ++w) acc += sm[w * BWD_WARP_FLOATS + (ly + 1) * 32 + lx];
+        acc += hand[ly * 33 + lx];
+        const int ix = X0 + lx, iy = Y0 + ly;
+        if (ix < n && iy < n) {
+            if (S == 1 && mode == BWD_PLAIN) s.ext_out[iy * n + ix] = s.dx * acc;
+            else s.bwd_part[(size_t)part * n * n + iy * n + ix] = acc;
+        }
     }
     __syncthreads();   // shared memory is reused by the next tile of a persistent block
 }
