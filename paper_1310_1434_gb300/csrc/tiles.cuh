@@ -232,7 +232,6 @@ __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile,
         const bool mixed = (e & VT_MIXED) != 0u;
 #pragma unroll 1
         for (int c0 = j0; c0 < j1; c0 += BWD_CHUNK) {
-            if (c0 != j0) fetch(e, v, c0 + lane);                       // ranges longer than a chunk
             {   // stage this lane's ray, tile- and walk-index-relative (see bwd_ray)
                 const bool col = mixed ? ro != 0 : colw;
                 const unsigned Mlo = __float_as_uint(rq.z);
@@ -249,7 +248,10 @@ __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile,
             }
             __syncwarp();
             const int cnt = min(BWD_CHUNK, j1 - c0);
-            if (c0 + BWD_CHUNK >= j1 && vn < V && mine(en)) fetch(en, vn, (int)(en & 0x3fffu) + lane);   // next view
+            // prefetch what is staged next while this chunk is swept: the
+            // range's next chunk, else the next view's first
+            if (c0 + BWD_CHUNK < j1) fetch(e, v, c0 + BWD_CHUNK + lane);
+            else if (vn < V && mine(en)) fetch(en, vn, (int)(en & 0x3fffu) + lane);
             if (!mixed) {
                 const unsigned kk = (e & VT_NEG) ? BWD_T - 1u - lane : (unsigned)lane;
 #pragma unroll 2
