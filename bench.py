@@ -137,8 +137,8 @@ def run_kernel(args):
     ell, _, Y = inputs.make_case(w)
     X = inputs.rasterize(g, ell)
     plan = air.Plan(g)
-    if args.kernel == "bwd":   # all views in one launch, as bench.py's roofline times it
-        air.air_plan_tune(plan, air.air_plan_config(plan)[0], 1)
+    if args.kernel == "bwd":   # the view split bench.py's roofline times
+        air.air_plan_tune(plan, air.air_plan_config(plan)[0], BWD_PARTS)
     Yd = torch.as_tensor(Y.astype(np.float32).ravel(), device="cuda")
     Xd = torch.as_tensor(X.astype(np.float32).ravel(), device="cuda")
     Zd = torch.empty_like(Yd)
@@ -523,10 +523,11 @@ def main():
     xout = torch.empty(g8.n ** 2, device=dev)
     air.air_backproject(p800, zin, xout)
     t_bwd_tuned = events_time(torch, stream, lambda: air.air_backproject(p800, zin, xout), 20)
-    # the roofline's launch: one k_op<OP_BWD> over all views (S = 1), the
-    # configuration `--kernel bwd` runs for the ncu capture
+    # the roofline's configuration: BWD_PARTS view parts in one k_op<OP_BWD>
+    # launch plus their sum (k_op<OP_BWD_FIN>), as `--kernel bwd` runs it for
+    # the ncu capture
     vpb, s_tuned, _ = air.air_plan_config(p800)
-    air.air_plan_tune(p800, vpb, 1)
+    air.air_plan_tune(p800, vpb, BWD_PARTS)
     air.air_backproject(p800, zin, xout)
     t_bwd = events_time(torch, stream, lambda: air.air_backproject(p800, zin, xout), 20)
     air.air_plan_tune(p800, vpb, s_tuned)
@@ -606,8 +607,8 @@ def main():
                       "fwd_hbm_gbs": alg_bytes / (t_fwd * 1e-3) / 1e9,
                       "bwd_hbm_gbs": alg_bytes / (t_bwd * 1e-3) / 1e9,
                       "hbm_frac_of_measured": alg_bytes / (t_bwd * 1e-3) / 1e9 / peaks["hbm_gbs"]},
-        "roofline": {"kernel": "backprojector (strip sweep, k_op<OP_BWD>, all views in one launch), "
-                               "512^2 / 800 views / 738 bins",
+        "roofline": {"kernel": f"backprojector (strip sweep, k_op<OP_BWD> over {BWD_PARTS} view parts "
+                               "+ k_op<OP_BWD_FIN>), 512^2 / 800 views / 738 bins",
                      "bound": "alu",
                      "achieved": nnz / (t_bwd * 1e-3) / 1e9,
                      "peak": seg_peak, "unit": "Gsegment/s",
@@ -626,6 +627,9 @@ def main():
         dist.destroy_process_group()
 
 
+# View parts of the backprojector launch the roofline times (2048 blocks of
+# 32 x 32 pixels at 512^2: 2.7 waves at 5 blocks per SM).
+BWD_PARTS = 8
 # Thread-instructions of the least a segment evaluation takes (overlap
 # compare, intersection length, gather, FMA, loop step): the divisor of the
 # issue-limited peak.
@@ -633,7 +637,7 @@ SEG_INST = 8
 # DRAM bytes (read + write) of one backprojector launch on the 512^2 / 800-view
 # slice, from the committed ncu capture of the current kernel (None when the
 # kernel has changed since).
-BWD_DRAM_BYTES_512_V800 = 22_537_728
+BWD_DRAM_BYTES_512_V800 = 20_083_200
 
 
 if __name__ == "__main__":
