@@ -55,6 +55,9 @@ GEOMS = {
     "ragged77_v31_b101": inputs.Geometry(77, 1.3, 31, 101, beta0=0.17),
     "short_scan64_b95": inputs.Geometry(64, 1.0, 45, 95, arc=1.3 * math.pi, beta0=-0.4),
     "tiny8_v12_b16": inputs.Geometry(8, 1.25, 12, 16),
+    # source 60 mm from the centre: wide fan angles, and most (view, tile)
+    # ray ranges of the backprojector hold both orientations or slope signs
+    "close_source45_v16_b64": inputs.Geometry(45, 1.1, 16, 64, dso_mm=60.0),
 }
 
 
@@ -129,11 +132,15 @@ def test_adjoint_identity_on_gpu_pair(name):
     assert abs(lhs - rhs) <= TOL_ADJ * scale
 
 
-@pytest.mark.parametrize("n,V,nb", [(8, 12, 16), (13, 9, 23)])
-def test_backprojector_is_exact_transpose(n, V, nb):
+@pytest.mark.parametrize("n,V,nb,dso,beta0", [(8, 12, 16, 850.0, 0.05), (13, 9, 23, 850.0, 0.05),
+                                               (45, 16, 64, 60.0, 0.0), (70, 10, 90, 70.0, 0.2)])
+def test_backprojector_is_exact_transpose(n, V, nb, dso, beta0):
     # column i of A (project e_i) and row r of A (backproject e_r) hold the
-    # same FP32 lengths, bit for bit
-    g = inputs.Geometry(n, 1.1, V, nb, beta0=0.05)
+    # same FP32 lengths, bit for bit.  45 and 70 span 2 x 2 and 3 x 3
+    # backprojector tiles (32 x 32 pixels) with a ragged last row and column;
+    # with the source this close, most (view, tile) ray ranges hold both ray
+    # orientations or both slope signs (46 of 64 and 53 of 90 pairs)
+    g = inputs.Geometry(n, 1.1, V, nb, beta0=beta0, dso_mm=dso)
     plan = air.Plan(g)
     m = V * nb
     E = torch.eye(n * n, device=DEV)
