@@ -3,9 +3,10 @@
 Tolerances are the ones the problem statement fixes for this path: a single A
 or A'^T application within 2e-6 relative L2 of the FP64 oracle, the GPU
 adjoint pair within 1e-5, and a full reconstruction within 1e-4.  Sizes span
-several tiles with ragged tails (77 x 77 pixels against 16 x 16 backprojector
-tiles, 31 x 101 rays against 256-ray projector tiles), a short scan, odd and
-even bin counts, and the full 512 x 512 / 738-bin slices of the benchmark.
+several tiles with ragged tails (77 x 77 pixels against 32 x 32 backprojector
+tiles, 31 x 101 rays against 256-ray projector tiles), a short scan, a source
+close to the image, odd and even bin counts, and the full 512 x 512 / 738-bin
+slices of the benchmark.
 """
 import math
 import os
