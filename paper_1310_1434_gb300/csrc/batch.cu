@@ -11,6 +11,7 @@
 // barrier in between, also captured in a graph.  It has one register and
 // shared-memory budget for every op, which costs occupancy on the projector
 // pair; it is kept for callers that want a single launch.
+#include <climits>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -291,20 +292,47 @@ extern "C" air_status air_solve_batch_persistent(int n, air_plan *const *plans, 
     BatchGraph &G = g_persistent;
     if (G.key != B.key || !G.exec) {
         release(G);
+        const int grid = persistent_grid(smem);
+        if (grid <= 0) return fail(AIR_ERR_CUDA, "batch set-up: no co-resident grid for the persistent kernel");
+        // per phase: prefix sums of the slices' tile counts, and the phase's
+        // first ticket (earlier phases' tiles plus one closing ticket per block)
+        const size_t np = B.nphases;
+        std::vector<int> tile_base(np * (n + 1));
+        std::vector<unsigned long long> phase_base(np);
+        unsigned long long tickets = 0;
+        for (size_t ph = 0; ph < np; ++ph) {
+            int *tb = &tile_base[ph * (n + 1)];
+            long long sum = 0;
+            tb[0] = 0;
+            for (int i = 0; i < n; ++i) {
+                sum += tiles_of(B.slices[i], prog[i * np + ph].op);
+                if (sum > INT_MAX) return fail(AIR_ERR_INVALID_ARG, "batch too large for one persistent launch");
+                tb[i + 1] = (int)sum;
+            }
+            phase_base[ph] = tickets;
+            tickets += (unsigned long long)sum + (unsigned long long)grid;
+        }
         const size_t b_slices = align_up(n * sizeof(SliceDesc), 256);
         const size_t b_prog = align_up(prog.size() * sizeof(Phase), 256);
-        if (cudaMalloc(&G.dmem, b_slices + b_prog + 256) != cudaSuccess) {
+        const size_t b_tb = align_up(tile_base.size() * sizeof(int), 256);
+        const size_t b_pb = align_up(phase_base.size() * sizeof(unsigned long long), 256);
+        if (cudaMalloc(&G.dmem, b_slices + b_prog + b_tb + b_pb + 256) != cudaSuccess) {
             cudaGetLastError();
             G.dmem = nullptr;
             return fail(AIR_ERR_OOM, "batch table allocation failed");
         }
         SliceDesc *d_slices = (SliceDesc *)G.dmem;
         Phase *d_prog = (Phase *)(G.dmem + b_slices);
-        G.ctl = (BatchCtl *)(G.dmem + b_slices + b_prog);
+        int *d_tb = (int *)(G.dmem + b_slices + b_prog);
+        unsigned long long *d_pb = (unsigned long long *)(G.dmem + b_slices + b_prog + b_tb);
+        G.ctl = (BatchCtl *)(G.dmem + b_slices + b_prog + b_tb + b_pb);
         cudaError_t e = cudaMemcpy(d_slices, B.slices.data(), n * sizeof(SliceDesc), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(d_prog, prog.data(), prog.size() * sizeof(Phase), cudaMemcpyHostToDevice);
-        const int grid = persistent_grid(smem);
-        if (e == cudaSuccess && grid <= 0) e = cudaErrorInvalidConfiguration;
+        if (e == cudaSuccess)
+            e = cudaMemcpy(d_tb, tile_base.data(), tile_base.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(d_pb, phase_base.data(), phase_base.size() * sizeof(unsigned long long),
+                           cudaMemcpyHostToDevice);
         if (e == cudaSuccess && !G.cap) e = cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) {
@@ -312,7 +340,8 @@ extern "C" air_status air_solve_batch_persistent(int n, air_plan *const *plans, 
             return fail(AIR_ERR_CUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
         }
         cudaError_t le = cudaMemsetAsync(G.ctl, 0, sizeof(BatchCtl), G.cap);
-        if (le == cudaSuccess) le = launch_persistent(d_slices, n, d_prog, (int)B.nphases, G.ctl, grid, smem, G.cap);
+        if (le == cudaSuccess)
+            le = launch_persistent(d_slices, n, d_prog, (int)B.nphases, d_tb, d_pb, G.ctl, grid, smem, G.cap);
         if ((s = end_capture(G, G.cap, le)) != AIR_OK) return s;
         G.key = B.key;
     }

@@ -239,24 +239,32 @@ __device__ bool grid_barrier(BatchCtl *ctl) {
     return ok != 0;
 }
 
+// Tiles are handed out in each phase from one global ticket counter, so
+// blocks that draw cheap tiles take more of them.  A block leaves a phase at
+// its first ticket past the phase's last tile; the phase's first ticket
+// (phase_base) counts those closing tickets, one per block, of every earlier
+// phase, and the grid barrier keeps the phases' tickets apart.
 __global__ void __launch_bounds__(AIR_THREADS, 5)
 k_persistent(const SliceDesc *__restrict__ slices, int nslices, const Phase *__restrict__ prog,
-             int nphases, BatchCtl *ctl) {
+             int nphases, const int *__restrict__ tile_base, const unsigned long long *__restrict__ phase_base,
+             BatchCtl *ctl) {
     extern __shared__ __align__(16) float sm[];
     __shared__ __align__(16) SliceDesc sd;
+    __shared__ long long drawn;
     int staged = -1;                  // slice whose descriptor sd holds
     for (int ph = 0; ph < nphases; ++ph) {
-        int si = 0, base = 0;
-        int ntile = nslices > 0 ? tiles_of(slices[0], prog[ph].op) : 0;
-        for (int t = blockIdx.x;; t += gridDim.x) {
-            while (si < nslices && t >= base + ntile) {
-                base += ntile;
-                ++si;
-                if (si < nslices) ntile = tiles_of(slices[si], prog[(size_t)si * nphases + ph].op);
-            }
-            if (si >= nslices) break;
+        const int *__restrict__ tb = tile_base + (size_t)ph * (nslices + 1);
+        const long long ntiles = tb[nslices];
+        int si = 0;
+        for (;;) {
+            if (threadIdx.x == 0) drawn = (long long)(atomicAdd(&ctl->ticket, 1ull) - phase_base[ph]);
+            __syncthreads();
+            const long long t = drawn;
+            __syncthreads();
+            if (t >= ntiles) break;
+            while (t >= tb[si + 1]) ++si;       // a block's tickets increase
             const Phase P = prog[(size_t)si * nphases + ph];
-            run_tile(stage_desc(slices, si, &sd, &staged), P.op, P.arg, t - base, sm);
+            run_tile(stage_desc(slices, si, &sd, &staged), P.op, P.arg, (int)(t - tb[si]), sm);
         }
         if (!grid_barrier(ctl)) return;
     }
@@ -273,8 +281,8 @@ int persistent_grid(size_t smem) {
 }
 
 cudaError_t launch_persistent(const SliceDesc *d_slices, int nslices, const Phase *d_prog,
-                              int nphases, BatchCtl *d_ctl, int grid, size_t smem,
-                              cudaStream_t st) {
+                              int nphases, const int *d_tile_base, const unsigned long long *d_phase_base,
+                              BatchCtl *d_ctl, int grid, size_t smem, cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(AIR_THREADS);
@@ -285,7 +293,8 @@ cudaError_t launch_persistent(const SliceDesc *d_slices, int nslices, const Phas
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_persistent, d_slices, nslices, d_prog, nphases, d_ctl);
+    return cudaLaunchKernelEx(&cfg, k_persistent, d_slices, nslices, d_prog, nphases, d_tile_base, d_phase_base,
+                              d_ctl);
 }
 
 }  // namespace air

@@ -30,10 +30,14 @@ struct BatchCtl {
     unsigned gen;        // grid barrier generation
     int error;           // AIR_ERR_TIMEOUT if a barrier wait gave up
     int pad;
+    unsigned long long ticket;   // tiles handed out so far (see k_persistent)
 };
+// tile_base: [nphases][nslices + 1] prefix sums of the slices' tile counts in
+// each phase; phase_base: [nphases] first ticket of each phase, the sum over
+// earlier phases of their tiles plus one closing ticket per block.
 cudaError_t launch_persistent(const SliceDesc *d_slices, int nslices, const Phase *d_prog,
-                              int nphases, BatchCtl *d_ctl, int grid, size_t smem,
-                              cudaStream_t st);
+                              int nphases, const int *d_tile_base, const unsigned long long *d_phase_base,
+                              BatchCtl *d_ctl, int grid, size_t smem, cudaStream_t st);
 // Largest co-resident grid of the persistent kernel for the given smem.
 int persistent_grid(size_t smem);
 
