@@ -51,6 +51,7 @@ constexpr int B_TILE = TN * TK * 2;             // bytes of one T piece tile
 constexpr int STAGE_BYTES = 3 * A_TILE + 3 * B_TILE;
 constexpr int GEMM_SMEM = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr long long WAIT_POLLS = 1ll << 24;     // bounded waits (~seconds with back-off)
+static_assert(TM * (TN + 1) * 4 <= STAGES * STAGE_BYTES, "the epilogue's table fits in the stage ring");
 
 struct TcRes {
     int kp = 0, np = 0;           // padded K (= bins) and N
@@ -278,9 +279,14 @@ k_ramp_gemm(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ C
     const int have = __syncthreads_and(mbar_wait(done, 0) ? 1 : 0);
     tc_fence_after();
     if (have && !abort_flag) {
-        const int row = m0 + warp * 32 + (threadIdx.x & 31);
+        // lane l of warp w holds row 32 w + l of the tile: it sums the four
+        // accumulators into a padded [row][TN + 1] table in the (now idle)
+        // stage ring, and the warp then adds its 32 rows to Z with lanes along
+        // the bins (coalesced)
+        const int lane = threadIdx.x & 31;
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
         const bool two_halves = nk > (nk + 1) / 2;   // accumulator 1 holds the second half of K
+        float *tile = reinterpret_cast<float *>(base) + (size_t)warp * 32 * (TN + 1);
         float a0[16], a1[16], a2[16], a3[16];
 #pragma unroll 1
         for (int c0 = 0; c0 < TN; c0 += 16) {
@@ -288,15 +294,25 @@ k_ramp_gemm(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ C
             tmem_ld16(lane_base + 1 * TN + c0, a1);
             tmem_ld16(lane_base + 2 * TN + c0, a2);
             tmem_ld16(lane_base + 3 * TN + c0, a3);
-            if (row < V) {
-                float *z = Z + (size_t)row * nb;
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int j = n0 + c0 + i;
-                    const float far = ((a3[i] + a2[i]) + (two_halves ? a1[i] : 0.f)) + a0[i];
-                    if (j < nb) z[j] += far;
-                }
-            }
+            for (int i = 0; i < 16; ++i)
+                tile[lane * (TN + 1) + c0 + i] = ((a3[i] + a2[i]) + (two_halves ? a1[i] : 0.f)) + a0[i];
+        }
+        __syncwarp();
+        // all of the warp's loads of Z first (one memory latency), then the stores
+        constexpr int PER = 32 * TN / 32;              // elements per lane
+        float zv[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int r = q / (TN / 32), c = lane + 32 * (q % (TN / 32));
+            const int row = m0 + warp * 32 + r, j = n0 + c;
+            zv[q] = (row < V && j < nb) ? Z[(size_t)row * nb + j] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int r = q / (TN / 32), c = lane + 32 * (q % (TN / 32));
+            const int row = m0 + warp * 32 + r, j = n0 + c;
+            if (row < V && j < nb) Z[(size_t)row * nb + j] = zv[q] + tile[r * (TN + 1) + c];
         }
     } else if (threadIdx.x == 0 && !have) {
         atomicExch(err, (int)AIR_ERR_TIMEOUT);
