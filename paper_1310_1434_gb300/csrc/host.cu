@@ -108,8 +108,8 @@ size_t plan_bytes_estimate(const air_geometry &g) {
     b += rays * 4 * 3;                           // z zc ybuf
     b += sizeof(CgState) + ((size_t)max_reduce_tiles(s) + 64) * 8 + 24 * 256;
     if (g.precision == AIR_PREC_BF16X3) {
-        const size_t kp = ((size_t)g.n_bins + 63) / 64 * 64;
-        b += (size_t)g.n_views * 3 * kp * 2 + 3 * kp * kp * 2 + 1024;
+        const size_t kp = ((size_t)g.n_bins + 127) / 128 * 128;   // split Y; both parities' T_far pieces
+        b += (size_t)g.n_views * 3 * kp * 2 + 3 * kp * kp + 1024;
     }
     return b;
 }

@@ -11,14 +11,17 @@
 //     (24 significant bits in all), and the six products of order >= 2^-16,
 //     Yh Th + Yh Tm + Ym Th + Ym Tm + Yh Tl + Yl Th, accumulated in FP32 in
 //     tensor memory (k_ramp_gemm).  The far taps are below c0/(pi^2 NEAR^2), so
-//     the split's rounding reaches Z only at the 1e-7 level.
+//     the split's rounding reaches Z only at the 1e-7 level.  The ramp's even
+//     lags are zero, so even output bins take only odd input bins and odd
+//     outputs only even inputs: the GEMM runs as two half-size products, one
+//     per output parity, with Y's columns ordered odd bins first, then even.
 //   The products are kept in four TMEM accumulators by magnitude -- Yh Th
 //   over the first and over the second half of K, the 2^-9-scale pair, and
 //   the 2^-18-scale triple -- and summed small to large in the epilogue, so
 //   that small terms are never added into a large running sum inside the
 //   tensor core, whose accumulation error then stays at the 1e-7 level too.
 //
-// k_ramp_gemm: one CTA per 128 views x 64 bins of Z, 128 threads.  Thread 0
+// k_ramp_gemm: one CTA per 128 views x 64 bins of one parity of Z, 128 threads.  Thread 0
 // streams 64-bin K chunks of the six operand pieces (3 of Y, 3 of T_far) with
 // TMA into a 3-stage ring of 128-byte-swizzled shared-memory tiles and issues
 // tcgen05.mma (M = 128, N = 64, K = 16) into a TMEM accumulator; the four
@@ -53,10 +56,16 @@ constexpr int GEMM_SMEM = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr long long WAIT_POLLS = 1ll << 24;     // bounded waits (~seconds with back-off)
 static_assert(TM * (TN + 1) * 4 <= STAGES * STAGE_BYTES, "the epilogue's table fits in the stage ring");
 
+// padded K (= N = bins): a multiple of 2 TK, so each parity's half is whole K chunks
+constexpr int KPAD = 2 * TK;
+static_assert(TN == TK, "both parities' halves of N are whole tiles");
+// column of input bin k within one split piece of Y: odd bins, then even bins
+__host__ __device__ inline int a_col(int k, int kh) { return (k & 1) ? (k >> 1) : kh + (k >> 1); }
+
 struct TcRes {
-    int kp = 0, np = 0;           // padded K (= bins) and N
-    __nv_bfloat16 *a = nullptr;   // [V][3 kp]: Yh | Ym | Yl per view
-    __nv_bfloat16 *b = nullptr;   // [3 np][kp]: Th, Tm, Tl of T_far (symmetric)
+    int kp = 0, np = 0;           // padded K (= bins) and N; kh = kp / 2 per parity
+    __nv_bfloat16 *a = nullptr;   // [V][3 kp]: Yh | Ym | Yl per view, each [odd bins | even bins]
+    __nv_bfloat16 *b = nullptr;   // [2 parities][3 pieces][np / 2][kp / 2]: T_far[2i + h][input bin of column l]
     float *near_taps = nullptr;   // [NEAR] c0 h[m], m < NEAR
     int *err = nullptr;           // device status word (0 = ok)
     char *mem = nullptr;
@@ -164,9 +173,10 @@ __global__ void __launch_bounds__(256) k_split_near(const float *__restrict__ Y,
         const float r1 = x - __bfloat162float(h);           // exact
         const __nv_bfloat16 m = __float2bfloat16_rn(r1);
         const float r2 = r1 - __bfloat162float(m);          // exact
-        a[k] = h;
-        a[kp + k] = m;
-        a[2 * kp + k] = __float2bfloat16_rn(r2);
+        const int col = a_col(k, kp / 2);
+        a[col] = h;
+        a[kp + col] = m;
+        a[2 * kp + col] = __float2bfloat16_rn(r2);
     }
     float *z = Z + (size_t)v * nb;
     for (int j = threadIdx.x; j < nb; j += blockDim.x) {
@@ -193,8 +203,13 @@ k_ramp_gemm(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ C
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
     __shared__ int abort_flag;
     const int warp = threadIdx.x >> 5;
-    const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
-    const int nk = kp / TK;
+    // output parity h: bins 2 i + h, i in [n0, n0 + TN); its input bins are
+    // the other parity's, Y columns [a0, a0 + kh) of each piece
+    const int kh = kp / 2, nh = np / 2, tiles_h = nh / TN;
+    const int par = blockIdx.y / tiles_h;
+    const int m0 = blockIdx.x * TM, n0 = (blockIdx.y - par * tiles_h) * TN;
+    const int a0 = par == 0 ? 0 : kh;
+    const int nk = kh / TK;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -228,8 +243,8 @@ k_ramp_gemm(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ C
             const int s = kc % STAGES;
             mbar_expect_tx(&full[s], STAGE_BYTES);
             for (int p = 0; p < 3; ++p) {
-                tma_load_2d(stage_a(s, p), &map_a, &full[s], p * kp + kc * TK, m0);
-                tma_load_2d(stage_b(s, p), &map_b, &full[s], kc * TK, p * np + n0);
+                tma_load_2d(stage_a(s, p), &map_a, &full[s], p * kp + a0 + kc * TK, m0);
+                tma_load_2d(stage_b(s, p), &map_b, &full[s], kc * TK, (par * 3 + p) * nh + n0);
             }
         };
         for (; issued < nk && issued < STAGES; ++issued) load(issued);
@@ -305,13 +320,13 @@ k_ramp_gemm(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ C
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
             const int r = q / (TN / 32), c = lane + 32 * (q % (TN / 32));
-            const int row = m0 + warp * 32 + r, j = n0 + c;
+            const int row = m0 + warp * 32 + r, j = 2 * (n0 + c) + par;
             zv[q] = (row < V && j < nb) ? Z[(size_t)row * nb + j] : 0.f;
         }
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
             const int r = q / (TN / 32), c = lane + 32 * (q % (TN / 32));
-            const int row = m0 + warp * 32 + r, j = n0 + c;
+            const int row = m0 + warp * 32 + r, j = 2 * (n0 + c) + par;
             if (row < V && j < nb) Z[(size_t)row * nb + j] = zv[q] + tile[r * (TN + 1) + c];
         }
     } else if (threadIdx.x == 0 && !have) {
@@ -370,9 +385,10 @@ air_status ramp_tc_create(air_plan *P) {
     const int V = P->geom.n_views, nb = P->geom.n_bins;
     TcRes *R = new (std::nothrow) TcRes();
     if (!R) return fail(AIR_ERR_OOM, "host allocation failed");
-    R->kp = (nb + TK - 1) / TK * TK;
-    R->np = (nb + TN - 1) / TN * TN;
-    const size_t ba = (size_t)V * 3 * R->kp * 2, bb = (size_t)3 * R->np * R->kp * 2;
+    R->kp = (nb + KPAD - 1) / KPAD * KPAD;
+    R->np = R->kp;
+    const int kh = R->kp / 2, nh = R->np / 2;
+    const size_t ba = (size_t)V * 3 * R->kp * 2, bb = (size_t)2 * 3 * nh * kh * 2;
     const size_t total = align_up(ba, 256) + align_up(bb, 256) + 256 + 256;
     if (cudaMalloc(&R->mem, total) != cudaSuccess) {
         cudaGetLastError();
@@ -386,20 +402,22 @@ air_status ramp_tc_create(air_plan *P) {
     // far band of c0 T split into three BF16 pieces (from FP64), near taps in FP32
     const double c0 = M_PI / ((double)V * P->geom.pixel_mm * P->geom.pixel_mm);
     auto h = [](int k) { return k == 0 ? 0.25 : (k % 2 ? -1.0 / (M_PI * M_PI * (double)k * (double)k) : 0.0); };
-    std::vector<uint16_t> hb((size_t)3 * R->np * R->kp, 0);
+    // B[(h 3 + p) nh + i][l]: piece p of c0 T_far[n][k] for output bin n = 2 i + h
+    // and the input bin k of column l among the other parity's bins
+    std::vector<uint16_t> hb((size_t)2 * 3 * nh * kh, 0);
     for (int n = 0; n < nb; ++n)
         for (int k = 0; k < nb; ++k) {
             const int lag = n > k ? n - k : k - n;
-            if (lag < NEAR) continue;
+            if (lag < NEAR || lag % 2 == 0) continue;      // the near band, and the zero even lags
             const double t = c0 * h(lag);
             const uint16_t p0 = bf16_rn((float)t);
             const double r1 = t - (double)bf16_f(p0);
             const uint16_t p1 = bf16_rn((float)r1);
             const double r2 = r1 - (double)bf16_f(p1);
             const uint16_t p2 = bf16_rn((float)r2);
-            hb[((size_t)0 * R->np + n) * R->kp + k] = p0;
-            hb[((size_t)1 * R->np + n) * R->kp + k] = p1;
-            hb[((size_t)2 * R->np + n) * R->kp + k] = p2;
+            const int par = n & 1, i = n >> 1, l = a_col(k, kh) - (par == 0 ? 0 : kh);
+            const uint16_t pc[3] = {p0, p1, p2};
+            for (int p = 0; p < 3; ++p) hb[((size_t)(par * 3 + p) * nh + i) * kh + l] = pc[p];
         }
     float nt[NEAR];
     double diag = 0.0;
@@ -413,7 +431,7 @@ air_status ramp_tc_create(air_plan *P) {
     if (e == cudaSuccess) e = cudaMemset(R->err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(R->a, 0, ba);
     const bool maps = e == cudaSuccess && make_map(&R->map_a, R->a, 3 * (uint64_t)R->kp, V, TK, TM) &&
-                      make_map(&R->map_b, R->b, R->kp, 3 * (uint64_t)R->np, TK, TN);
+                      make_map(&R->map_b, R->b, kh, 2 * 3 * (uint64_t)nh, TK, TN);
     if (e == cudaSuccess) {
         e = cudaFuncSetAttribute(k_ramp_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
         if (e == cudaSuccess)   // the largest any plan needs: the limit is per kernel, not per plan
@@ -450,7 +468,7 @@ air_status ramp_tc_apply(const air_plan *P, const float *src, float *dst, const 
                                                                    R->kp, cg, respect_stop);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {
-        dim3 grid((V + TM - 1) / TM, R->np / TN);
+        dim3 grid((V + TM - 1) / TM, R->np / TN);   // both parities: 2 x (np / 2) / TN
         k_ramp_gemm<<<grid, 128, GEMM_SMEM, st>>>(R->map_a, R->map_b, dst, V, nb, R->kp, R->np, cg, respect_stop,
                                                   R->err);
         e = cudaGetLastError();
