@@ -81,12 +81,13 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // -------------------------------------------------------------------- plan
 namespace air {
 // Backprojector view parts of a slice: enough (pixel tile, part) blocks for
-// ~4 waves of 6 resident blocks per SM, at most one part per view.
+// about 12 per SM (2.4 waves at 5 resident blocks), at most one part per
+// view.  The autotuner starts from this and tries up to twice as many.
 int choose_bwd_parts(const SliceDesc &s) {
     int sms = 148, dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaGetLastError();
-    const int txy = tiles_bwd_xy(s), target = 4 * 6 * sms;
+    const int txy = tiles_bwd_xy(s), target = 2 * 6 * sms;
     const int S = (target + txy - 1) / txy;
     return S < 1 ? 1 : (S > s.V ? s.V : S);
 }
