@@ -179,12 +179,17 @@ __global__ void __launch_bounds__(256) k_split_near(const float *__restrict__ Y,
         a[2 * kp + col] = __float2bfloat16_rn(r2);
     }
     float *z = Z + (size_t)v * nb;
+    float t[NEAR / 2];                                  // the odd-lag taps, in registers
+#pragma unroll
+    for (int q = 0; q < NEAR / 2; ++q) t[q] = __ldg(taps + 2 * q + 1);
     for (int j = threadIdx.x; j < nb; j += blockDim.x) {
         const float c = P[NEAR + j];
         float acc = 0.f;
-#pragma unroll 8
-        for (int m = 1; m < NEAR; m += 2)
-            acc = fmaf(taps[m], __fadd_rn(__fsub_rn(P[NEAR + j - m], c), __fsub_rn(P[NEAR + j + m], c)), acc);
+#pragma unroll
+        for (int q = 0; q < NEAR / 2; ++q) {
+            const int m = 2 * q + 1;
+            acc = fmaf(t[q], __fadd_rn(__fsub_rn(P[NEAR + j - m], c), __fsub_rn(P[NEAR + j + m], c)), acc);
+        }
         z[j] = fmaf(near_diag, c, acc);
     }
 }
