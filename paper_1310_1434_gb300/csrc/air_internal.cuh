@@ -122,7 +122,7 @@ struct SliceDesc {
     // solver state (plan-owned workspace)
     float *x, *r, *p, *q, *rhs0, *g;   // n*n
     float *g2;                         // n*n: g of the previous outer step (g is double-buffered)
-    float *xp, *xt;                    // n*(n+2) each: zero-padded copy and transpose of the projector's input
+    float *xp, *xt;                    // n*(n+1) float2 each: pair copies {X[r], X[r+1]} of the projector's input and its transpose
     float *bwd_part;                   // bwd_parts * n*n: the backprojector's per-view-part sums
     int bwd_parts;                     // S: views split over S blocks per pixel tile (tuned)
     int fwd_vpb;                       // projector tile: views per block (1, 2, 4, 8; tuned)

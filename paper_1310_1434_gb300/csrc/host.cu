@@ -104,7 +104,7 @@ size_t plan_bytes_estimate(const air_geometry &g) {
     const size_t parts = (size_t)std::min(g.n_views, 2 * choose_bwd_parts(s));
     size_t b = rays * sizeof(RayFx) + (size_t)g.n_views * tiles_bwd_xy(s) * 4 + (size_t)g.n_bins * 4;
     b += nn * 4 * (7 + parts + 18 + 1);          // x r p q rhs0 g g', parts, b b2, xbuf
-    b += (size_t)g.n * (g.n + 2) * 4 * 2;        // xp xt
+    b += (size_t)g.n * (g.n + 1) * 8 * 2;        // xp xt (pairs)
     b += (size_t)g.n_views * 8 + (size_t)g.n_bins * 8;   // FBP tables
     b += rays * 4 * 3;                           // z zc ybuf
     b += sizeof(CgState) + ((size_t)max_reduce_tiles(s) + 64) * 8 + 24 * 256;
@@ -471,7 +471,7 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     // carve one allocation
     struct Piece { void **dst; size_t bytes; };
     float *x, *r, *p, *q, *rhs0, *gg, *gg2, *b, *b2, *z, *zc, *ybuf, *xbuf, *xp, *xt, *bpart;
-    const size_t npad = (size_t)n * (n + 2);   // padded copies of the projector's input
+    const size_t npad = (size_t)n * (n + 1) * 2;   // pair copies of the projector's input (floats)
     RayFx *ray;
     unsigned *vt;
     float2 *fview;

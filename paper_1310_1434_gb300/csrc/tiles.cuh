@@ -15,38 +15,42 @@ namespace air {
 // and, when the low word lo32 + Ma wraps past 2^32, row r0 + 1 too.  The
 // overlaps are ov1 = (lo32 + Ma) mod 2^32 with the next row (0 without a
 // wrap) and ov0 = Ma - ov1 with row r0, and the lengths ov * c (see RayFx).
-// The walk reads zero-padded copies of the image (entry -1 and n of every
-// row are zero, and r0 lies in [-1, n-1] on the walk range), so it needs no
-// bounds checks; rays walking columns read the transposed copy so that the
-// rays of a warp read neighbouring addresses.  The per-ray factor c is taken
-// out of the sum: a unit input still gives the entry ov * c exactly.
+// The walk reads pair copies of the image: row k holds the n + 1 pairs
+// {X[r], X[r + 1]} for r = -1 .. n-1 (X[-1] = X[n] = 0), so one aligned
+// 8-byte load gives both rows a column step can touch; r0 lies in [-1, n-1]
+// on the walk range, so the walk needs no bounds checks.  Rays walking
+// columns read the transposed copy so that the rays of a warp read
+// neighbouring addresses.  The per-ray factor c is taken out of the sum: a
+// unit input still gives the entry ov * c exactly.
 // ======================================================================
-__host__ __device__ inline int pad_ld(int n) { return n + 2; }   // row stride of the padded copies
+__host__ __device__ inline int pair_ld(int n) { return n + 1; }   // pairs per row of the pair copies
 
 // One column of the walk: the overlaps of the span [lo, lo + Ma] with row r0
-// and (when lo32 + Ma wraps past 2^32) row r0 + 1, times the pixel values.
-__device__ __forceinline__ void fx_step(long long &lo, const float *__restrict__ &row, long long M, unsigned Ma,
+// and (when lo32 + Ma wraps past 2^32) row r0 + 1, times the pixel pair
+// {X[r0], X[r0 + 1]} read with one 8-byte load; without a wrap ov1 = 0.
+__device__ __forceinline__ void fx_step(long long &lo, const float2 *__restrict__ &row, long long M, unsigned Ma,
                                         int ld, float &a0, float &a1) {
     const int r0 = (int)(lo >> 32);
     const unsigned t = (unsigned)lo + Ma;
     const unsigned ov1 = t < Ma ? t : 0u;      // t < Ma iff the add wrapped
     const unsigned ov0 = Ma - ov1;
-    a0 = fmaf(__uint2float_rn(ov0), __ldg(row + r0), a0);
-    if (ov1 != 0u) a1 = fmaf(__uint2float_rn(ov1), __ldg(row + r0 + 1), a1);
+    const float2 xx = __ldg(row + r0 + 1);
+    a0 = fmaf(__uint2float_rn(ov0), xx.x, a0);
+    a1 = fmaf(__uint2float_rn(ov1), xx.y, a1);
     lo += M;
     row += ld;
 }
 
-// Sum over the walk of ov * X (without c), from the padded copies.
+// Sum over the walk of ov * X (without c), from the pair copies.
 // Consecutive columns alternate between two accumulator pairs: four FP32
 // accumulators of about a quarter of the terms each (two independent FMA
 // chains), which keeps the ray sum's rounding error within the
 // single-application bound for images up to 1024^2.
-__device__ __forceinline__ float fx_ray(const float *__restrict__ XP, const float *__restrict__ XTP, int n,
+__device__ __forceinline__ float fx_ray(const float2 *__restrict__ XP, const float2 *__restrict__ XTP, int n,
                                         const RayFx &r) {
     const int k0 = r.kk & 0xffff, k1 = r.kk >> 16;
-    const int ld = pad_ld(n);
-    const float *__restrict__ row = (r.o ? XTP : XP) + (size_t)k0 * ld + 1;   // row k, entry 0
+    const int ld = pair_ld(n);
+    const float2 *__restrict__ row = (r.o ? XTP : XP) + (size_t)k0 * ld;   // row k, pair {X[-1], X[0]}
     const long long M = ray_M(r);
     const unsigned Ma = r.Ma;
     long long lo = r.L0 + (long long)k0 * M;
@@ -73,16 +77,19 @@ __device__ __forceinline__ void tile_fwd(const SliceDesc &s, int arg, int tile) 
     if (v >= s.V || j >= s.nb) return;
     const int idx = v * s.nb + j;
     const RayFx r = s.ray[idx];
-    dst[idx] = s.dx * (fabsf(r.cs) * fx_ray(s.xp, s.xt, s.n, r));
+    dst[idx] = s.dx * (fabsf(r.cs) * fx_ray(reinterpret_cast<const float2 *>(s.xp),
+                                            reinterpret_cast<const float2 *>(s.xt), s.n, r));
 }
 
-// xp = src and xt = transpose(src), both zero-padded (row stride n + 2,
-// entry -1 at offset 0), in 32 x 32 tiles through shared memory; runs
-// before every projection.  The pads are zeroed once with the plan.
+// xp and xt: the pair copies of src and of its transpose (pair r + 1 of a
+// row holds {X[r], X[r + 1]}, so each pixel is written as the first half of
+// one pair and the second half of the one before), in 32 x 32 tiles through
+// shared memory; runs before every projection.  The two ends that hold no
+// pixel (X[-1] and X[n]) are zeroed once with the plan.
 __device__ __forceinline__ void tile_transpose(const SliceDesc &s, int arg, int tile, float *sm) {
     if (arg == SRC_P && s.cg->stop) return;
     const float *src = arg == SRC_X ? s.x : (arg == SRC_P ? s.p : s.ext_in);
-    const int n = s.n, tpr = (n + 31) / 32, ld = pad_ld(n);
+    const int n = s.n, tpr = (n + 31) / 32, ld = 2 * pair_ld(n);   // floats per row of pairs
     const int x0 = (tile % tpr) * 32, y0 = (tile / tpr) * 32;
     float(*t)[33] = reinterpret_cast<float(*)[33]>(sm);
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -90,11 +97,18 @@ __device__ __forceinline__ void tile_transpose(const SliceDesc &s, int arg, int 
         if (y0 + yy < n && x0 + tx < n) {
             const float v = src[(size_t)(y0 + yy) * n + x0 + tx];
             t[yy][tx] = v;
-            s.xp[(size_t)(y0 + yy) * ld + 1 + x0 + tx] = v;
+            float *row = s.xp + (size_t)(y0 + yy) * ld;       // X[x] is pair x+1 .x and pair x .y
+            row[2 * (x0 + tx + 1)] = v;
+            row[2 * (x0 + tx) + 1] = v;
         }
     __syncthreads();
     for (int xx = ty; xx < 32; xx += AIR_THREADS / 32)
-        if (x0 + xx < n && y0 + tx < n) s.xt[(size_t)(x0 + xx) * ld + 1 + y0 + tx] = t[tx][xx];
+        if (x0 + xx < n && y0 + tx < n) {
+            float *row = s.xt + (size_t)(x0 + xx) * ld;
+            const float v = t[tx][xx];
+            row[2 * (y0 + tx + 1)] = v;
+            row[2 * (y0 + tx) + 1] = v;
+        }
     __syncthreads();
 }
 
