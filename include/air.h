@@ -136,9 +136,10 @@ AIR_API air_status air_filtered_backproject(const air_plan *plan, const float *Y
  * thread that holds a lock which another thread's allocation would need.
  * The paper has no counterpart; this is a deployment variant.
  *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
- *     Its one scratch buffer, the filtered sinogram, is a static device array
- *     of 2^20 floats (4 MB) that every GPU loading the library keeps until
- *     the process exits.
+ *     Its one scratch buffer is a static device array of 2^22 floats (16 MB)
+ *     that every GPU loading the library keeps until the process exits: the
+ *     filtered sinogram, then as many of the backprojector's view parts
+ *     (n*n floats each, up to the plan's tuned split) as fit beside it.
  *   - n_views * n_bins must be <= 2^20 (1,048,576); larger plans get
  *     AIR_ERR_INVALID_ARG.
  *   - The first call on a device looks up the array's device address

@@ -2,8 +2,9 @@
 // callers that must not allocate device memory at call time -- for example
 // code running under a device-memory budget that forbids cudaMalloc after
 // start-up, or a host thread that holds a lock another thread needs to
-// allocate.  Its only scratch, the filtered sinogram C Y, lives in the
-// file-scope device array below instead of in plan or caller memory.
+// allocate.  Its only scratch -- the filtered sinogram C Y and the
+// backprojector's per-view-part images -- lives in the file-scope device
+// array below instead of in plan or caller memory.
 #include <mutex>
 #include <string>
 
@@ -14,14 +15,18 @@ using namespace air;
 namespace {
 
 // Largest filtered sinogram the static scratch holds: n_views * n_bins.
-constexpr size_t NOALLOC_MAX_SAMPLES = size_t(1) << 20;   // 4 MB of float
+constexpr size_t NOALLOC_MAX_SAMPLES = size_t(1) << 20;
+// The whole array (16 MB of float): the filtered sinogram, then as many of
+// the backprojector's view parts (n * n floats each) as fit, up to the plan's
+// tuned split.
+constexpr size_t NOALLOC_FLOATS = size_t(1) << 22;
 
 // Every GPU that loads this library reserves this array until the process
 // exits.  All calls on a device share it and it keeps the last call's
 // contents; every element a call reads was written earlier by the same call
-// (the filter writes all n_views * n_bins samples), so nothing needs
-// clearing.  Calls that overlap on the GPU race on it.
-static __device__ __align__(256) float g_fbp_scratch[NOALLOC_MAX_SAMPLES];
+// (the filter writes all n_views * n_bins samples, each view part all n * n
+// pixels), so nothing needs clearing.  Calls that overlap on the GPU race on it.
+static __device__ __align__(256) float g_fbp_scratch[NOALLOC_FLOATS];
 
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
@@ -71,11 +76,17 @@ extern "C" air_status air_filtered_backproject_noalloc(const air_plan *P, const 
     d.ext_out = scratch;
     cudaError_t e = launch_op(OP_RAMP, d, RSRC_EXT, s);
     if (e == cudaSuccess) {
-        d.ext_in = scratch;  // X = A^T (C Y), in one view part: written straight to X
+        // X = A^T (C Y) over S view parts that fit beside C Y (one part is
+        // written straight to X), their sum by the finish op
+        const size_t nn = (size_t)P->geom.n * P->geom.n, off = align_up(samples, 64);
+        int parts = P->desc.bwd_parts;
+        while (parts > 1 && off + (size_t)parts * nn > NOALLOC_FLOATS) --parts;
+        d.ext_in = scratch;
         d.ext_out = X;
-        d.bwd_parts = 1;
-        d.bwd_part = nullptr;
+        d.bwd_parts = parts;
+        d.bwd_part = parts > 1 ? scratch + off : nullptr;
         e = launch_op(OP_BWD, d, BWD_PLAIN, s);
+        if (e == cudaSuccess && parts > 1) e = launch_op(OP_BWD_FIN, d, BWD_PLAIN, s);
     }
     if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("filtered backprojection: ") + cudaGetErrorString(e));
     return AIR_OK;

@@ -2,8 +2,8 @@
 
 Some callers cannot call cudaMalloc when they need the operator, e.g. code
 that runs under a fixed device-memory budget with allocation closed after
-start-up.  This entry point keeps its scratch (the filtered sinogram) in a
-static device array.  The test calls it through the C ABI twice in a row on
+start-up.  This entry point keeps its scratch (the filtered sinogram and the
+backprojector's view parts) in a static device array.  The test calls it through the C ABI twice in a row on
 different data, so the second call reuses the array the first one left
 behind, and checks each result against air_filtered_backproject within the
 single-application tolerance (2e-6 relative L2).  It is collected last.
@@ -41,6 +41,29 @@ def test_noalloc_matches_filtered_backproject_twice():
         b = X_ref.cpu().numpy().astype(np.float64)
         assert np.all(np.isfinite(a))
         assert np.linalg.norm(a - b) <= TOL * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("n,V,nb,parts", [(512, 200, 738, 1), (1024, 32, 1476, 4)])
+def test_noalloc_view_parts(n, V, nb, parts):
+    # one view part (written straight to X), and a split larger than the
+    # static scratch holds beside C Y at 1024^2 (four parts, three fit)
+    lib = air.load()
+    g = inputs.Geometry(n, 512 * 0.8 / n, V, nb)
+    plan = air.Plan(g)
+    air.air_plan_tune(plan, air.air_plan_config(plan)[0], parts)
+    ell = inputs.random_phantom(g, 23, 8, 4)
+    Yd = torch.as_tensor(inputs.ellipse_line_integrals(g, ell).astype(np.float32).ravel(), device="cuda")
+    X_ref = torch.empty(g.n * g.n, device="cuda")
+    X_na = torch.full((g.n * g.n,), float("nan"), device="cuda")
+    air.air_filtered_backproject(plan, Yd, X_ref)
+    st = lib.air_filtered_backproject_noalloc(plan.handle, Yd.data_ptr(), X_na.data_ptr(),
+                                              torch.cuda.current_stream().cuda_stream)
+    assert st == air.AIR_OK, air.last_error()
+    torch.cuda.synchronize()
+    a = X_na.cpu().numpy().astype(np.float64)
+    b = X_ref.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(a))
+    assert np.linalg.norm(a - b) <= TOL * np.linalg.norm(b)
 
 
 def test_noalloc_rejects_a_plan_larger_than_its_scratch():
