@@ -304,7 +304,8 @@ air_status build_tables(const air_geometry &g, double dg, int ntxy, HostTables &
     // centred) and the central-ray direction; per ray the fixed-point line
     std::vector<RayFx> &hray = T.ray;
     hray.resize(rays);
-    std::vector<double4> hsrc(V);   // per view: source (pixel units, centred), central direction
+    struct ViewSrc { double x, y, z, w; };   // source (pixel units, centred), central direction
+    std::vector<ViewSrc> hsrc(V);
     std::vector<float> &htaps = T.taps;
     htaps.resize(nb);
     const double inv_dx = 1.0 / g.pixel_mm;
@@ -312,7 +313,7 @@ air_status build_tables(const air_geometry &g, double dg, int ntxy, HostTables &
         const double beta = g.beta0 + g.arc * (double)v / (double)V;
         const double cb = std::cos(beta), sb = std::sin(beta);
         const double Sx = g.dso_mm * cb, Sy = g.dso_mm * sb;
-        hsrc[v] = make_double4(Sx * inv_dx, Sy * inv_dx, -cb, -sb);
+        hsrc[v] = ViewSrc{Sx * inv_dx, Sy * inv_dx, -cb, -sb};
         for (int j = 0; j < nb; ++j) {
             const double gamma = ((double)j - 0.5 * (nb - 1)) * dg;
             const double th = beta + M_PI + gamma;
@@ -350,7 +351,7 @@ air_status build_tables(const air_geometry &g, double dg, int ntxy, HostTables &
         std::vector<int> chg(nb);   // number of changes of orientation or slope sign among rays 0..j
         const double jm = 0.5 * (nb - 1);
         for (int v = 0; v < V; ++v) {
-            const double4 w = hsrc[v];
+            const ViewSrc w = hsrc[v];
             for (int iy = 0; iy <= tpr; ++iy)
                 for (int ix = 0; ix <= tpr; ++ix) {
                     const double px = std::min(ix * BWD_T, n) - 0.5 * n, py = std::min(iy * BWD_T, n) - 0.5 * n;
