@@ -72,19 +72,22 @@ def test_grouped_batch_mixes_precisions():
         assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b), w.name
 
 
-def test_config2_batch_of_64_uneven_slices():
+@pytest.mark.parametrize("form", ["grouped", "persistent"])
+def test_config2_batch_of_64_uneven_slices(form):
     """The 64-slice batch of uneven geometry (256^2/200 views, 512^2/400,
-    512^2/800 and 768^2/800, seeds 100..163) through the grouped batch: every
-    slice equals its single-slice solve, and one slice of each shape matches
-    the FP64 oracle (fewer iterations than the benchmark's 30 x 8, which the
-    oracle cannot run 64 times)."""
+    512^2/800 and 768^2/800, seeds 100..163), grouped and persistent (whose
+    blocks draw tiles from one ticket counter across all 64 slices): every
+    slice equals its single-slice solve, and (grouped) one slice of each shape
+    matches the FP64 oracle (fewer iterations than the benchmark's 30 x 8,
+    which the oracle cannot run 64 times)."""
     import oracle
     ws = inputs.batch_workloads(64, n_outer=2, n_cg=2)
+    solve = air.air_solve_batch if form == "grouped" else air.air_solve_batch_persistent
     Ys = [torch.as_tensor(f32(inputs.make_case(w)[2]).ravel(), device=DEV) for w in ws]
     plans = [air.Plan(w.geom) for w in ws]
     Xb = [torch.full((w.geom.n ** 2,), float("nan"), device=DEV) for w in ws]
-    air.air_solve_batch(plans, Ys, [w.lam for w in ws], [w.mu for w in ws], [w.n_outer for w in ws],
-                        [w.n_cg for w in ws], Xb)
+    solve(plans, Ys, [w.lam for w in ws], [w.mu for w in ws], [w.n_outer for w in ws],
+          [w.n_cg for w in ws], Xb)
     for i, (w, p, Y, xb) in enumerate(zip(ws, plans, Ys, Xb)):
         xs = torch.empty_like(xb)
         air.air_solve(p, Y, w.lam, w.mu, w.n_outer, w.n_cg, xs)
@@ -92,7 +95,7 @@ def test_config2_batch_of_64_uneven_slices():
         a, b = xb.cpu().numpy().astype(np.float64), xs.cpu().numpy().astype(np.float64)
         assert np.all(np.isfinite(a))
         assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b), w.name
-        if i < 4:   # one of each shape against the oracle
+        if i < 4 and form == "grouped":   # one of each shape against the oracle
             og = oracle.Geometry(**{k: getattr(w.geom, k) for k in oracle.Geometry.__dataclass_fields__})
             ref = oracle.solve(og, Y.cpu().numpy().astype(np.float64), w.lam, w.mu, w.n_outer, w.n_cg)
             assert np.linalg.norm(a - ref.ravel()) <= 1e-4 * np.linalg.norm(ref), w.name
