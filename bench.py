@@ -138,7 +138,8 @@ def run_kernel(args):
     X = inputs.rasterize(g, ell)
     plan = air.Plan(g)
     if args.kernel == "bwd":   # the view split bench.py's roofline times
-        air.air_plan_tune(plan, air.air_plan_config(plan)[0], BWD_PARTS)
+        vpb, _, s_max = air.air_plan_config(plan)
+        air.air_plan_tune(plan, vpb, min(BWD_PARTS, s_max))
     Yd = torch.as_tensor(Y.astype(np.float32).ravel(), device="cuda")
     Xd = torch.as_tensor(X.astype(np.float32).ravel(), device="cuda")
     Zd = torch.empty_like(Yd)
@@ -526,8 +527,9 @@ def main():
     # the roofline's configuration: BWD_PARTS view parts in one k_op<OP_BWD>
     # launch plus their sum (k_op<OP_BWD_FIN>), as `--kernel bwd` runs it for
     # the ncu capture
-    vpb, s_tuned, _ = air.air_plan_config(p800)
-    air.air_plan_tune(p800, vpb, BWD_PARTS)
+    vpb, s_tuned, s_max = air.air_plan_config(p800)
+    s_rf = min(BWD_PARTS, s_max)
+    air.air_plan_tune(p800, vpb, s_rf)
     air.air_backproject(p800, zin, xout)
     t_bwd = events_time(torch, stream, lambda: air.air_backproject(p800, zin, xout), 20)
     air.air_plan_tune(p800, vpb, s_tuned)
@@ -607,7 +609,7 @@ def main():
                       "fwd_hbm_gbs": alg_bytes / (t_fwd * 1e-3) / 1e9,
                       "bwd_hbm_gbs": alg_bytes / (t_bwd * 1e-3) / 1e9,
                       "hbm_frac_of_measured": alg_bytes / (t_bwd * 1e-3) / 1e9 / peaks["hbm_gbs"]},
-        "roofline": {"kernel": f"backprojector (strip sweep, k_op<OP_BWD> over {BWD_PARTS} view parts "
+        "roofline": {"kernel": f"backprojector (strip sweep, k_op<OP_BWD> over {s_rf} view parts "
                                "+ k_op<OP_BWD_FIN>), 512^2 / 800 views / 738 bins",
                      "bound": "alu",
                      "achieved": nnz / (t_bwd * 1e-3) / 1e9,
