@@ -104,9 +104,23 @@ AIR_API air_status air_plan_config(const air_plan *plan, int *fwd_views_per_bloc
 
 /* Status recorded on the device by the plan's kernels: AIR_OK, or
  * AIR_ERR_TIMEOUT if a bounded wait inside a kernel gave up (the kernel then
- * returned without its result).  Synchronises the device.  The status word is
- * cleared by air_plan_create only. */
+ * returned without its result).  Synchronises the device.  Reading a status
+ * other than AIR_OK clears it, so a later call reports only later failures. */
 AIR_API air_status air_plan_status(const air_plan *plan);
+
+/* Diagnostic control of the bounded device-side waits; the paper has no
+ * counterpart.  Every spin-wait inside the library's kernels gives up after a
+ * poll budget (a few seconds) and records AIR_ERR_TIMEOUT instead of hanging:
+ * the persistent batch kernel's grid barrier (reported by
+ * air_solve_batch_persistent) and the tensor-core filter's wait for a
+ * pipeline stage's operands (reported by air_plan_status and by the calls
+ * that check it).  polls >= 0 sets that budget for kernels launched
+ * afterwards on the current device, polls < 0 restores the default; with 0 a
+ * wait gives up without polling, which lets a test drive the failure path.
+ * The waits with which a kernel that gave up drains its own asynchronous
+ * copies and tensor-core operations before it exits keep the default budget.
+ * Synchronous; process-wide for the device. */
+AIR_API air_status air_set_wait_budget(int64_t polls);
 /* Device bytes the plan holds (tables + workspace). */
 AIR_API size_t     air_plan_bytes(const air_plan *plan);
 
@@ -136,14 +150,19 @@ AIR_API air_status air_filtered_backproject(const air_plan *plan, const float *Y
  * thread that holds a lock which another thread's allocation would need.
  * The paper has no counterpart; this is a deployment variant.
  *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
- *     Its one scratch buffer is a static device array of 2^22 floats (16 MB)
- *     that every GPU loading the library keeps until the process exits: the
- *     filtered sinogram, then as many of the backprojector's view parts
+ *     Its one scratch buffer is a static device array of 2^22 floats (16 MB):
+ *     the filtered sinogram, then as many of the backprojector's view parts
  *     (n*n floats each, up to the plan's tuned split) as fit beside it.
+ *   - CUDA allocates that array when it first loads the code that holds it
+ *     on a device.  air_plan_create does so and records the array's device
+ *     address (cudaGetSymbolAddress), so every device on which a plan has
+ *     been created holds the 16 MB until the process exits: create the plans
+ *     before a device-memory budget closes.  A call on a device where no plan
+ *     was created looks the address up itself (loading the code then); make
+ *     such a call before any stream capture.  After a cudaDeviceReset, create
+ *     a plan again on that device before calling.
  *   - n_views * n_bins must be <= 2^20 (1,048,576); larger plans get
  *     AIR_ERR_INVALID_ARG.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
  *   - All calls on a device share the array; calls that overlap on the GPU
  *     race.  Each call writes every sample it later reads.
  *   - Applies the FP32 filter whatever the plan's precision; Y, X as for

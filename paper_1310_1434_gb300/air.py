@@ -27,7 +27,7 @@ PREC_FP32, PREC_BF16X3 = 0, 1
 
 # every symbol include/air.h declares
 EXPORTS = ["air_last_error", "air_plan_create", "air_plan_destroy", "air_plan_bytes", "air_plan_status",
-           "air_plan_tune", "air_plan_config",
+           "air_set_wait_budget", "air_plan_tune", "air_plan_config",
            "air_project",
            "air_filter", "air_backproject", "air_filtered_backproject", "air_filtered_backproject_noalloc",
            "air_framelet", "air_shrink",
@@ -77,6 +77,7 @@ def load(build_if_missing: bool = False):
         "air_plan_destroy": (i32, [P]),
         "air_plan_bytes": (ctypes.c_size_t, [P]),
         "air_plan_status": (i32, [P]),
+        "air_set_wait_budget": (i32, [ctypes.c_int64]),
         "air_plan_tune": (i32, [P, i32, i32]),
         "air_plan_config": (i32, [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "air_project": (i32, [P, P, P, P]),
@@ -201,6 +202,11 @@ def air_plan_destroy(plan: Plan):
 
 def air_plan_status(plan: Plan):
     _check(load().air_plan_status(plan.handle), "air_plan_status")
+
+
+def air_set_wait_budget(polls: int):
+    """Poll budget of the kernels' bounded waits on the current device (< 0: the default)."""
+    _check(load().air_set_wait_budget(int(polls)), "air_set_wait_budget")
 
 
 def air_plan_tune(plan: Plan, fwd_views_per_block: int, bwd_view_parts: int):

@@ -116,11 +116,14 @@ air_status run_cached(BatchGraph &G, cudaStream_t st) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("batch solve: ") + cudaGetErrorString(e));
     if (ctl.error != 0) return fail(AIR_ERR_TIMEOUT, "a grid barrier of the batch kernel timed out");
+    // every tensor-core plan's status is read (which clears it), the first
+    // failure reported
+    air_status first = AIR_OK;
     for (const air_plan *p : G.tc_plans) {
-        air_status s = air_plan_status(p);
-        if (s != AIR_OK) return s;
+        const air_status s = air_plan_status(p);
+        if (first == AIR_OK && s != AIR_OK) first = s;
     }
-    return AIR_OK;
+    return first == AIR_OK ? AIR_OK : fail(first, "a bounded wait in a slice's tensor-core filter gave up");
 }
 
 air_status end_capture(BatchGraph &G, cudaStream_t cs, cudaError_t launch_err) {

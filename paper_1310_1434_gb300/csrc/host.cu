@@ -564,6 +564,7 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
         }
     }
     air_status st = autotune(P);
+    if (st == AIR_OK) st = noalloc_prepare();
     if (st != AIR_OK) {
         ramp_tc_destroy(P);
         cudaFree(mem);
@@ -617,6 +618,17 @@ extern "C" air_status air_plan_config(const air_plan *P, int *fwd_views_per_bloc
     if (fwd_views_per_block) *fwd_views_per_block = P->desc.fwd_vpb;
     if (bwd_view_parts) *bwd_view_parts = P->desc.bwd_parts;
     if (bwd_view_parts_max) *bwd_view_parts_max = P->bwd_parts_max;
+    return AIR_OK;
+}
+
+extern "C" air_status air_set_wait_budget(int64_t polls) {
+    const long long v = polls < 0 ? -1ll : (long long)polls;
+    cudaError_t e = set_barrier_budget(v);
+    if (e == cudaSuccess) e = ramp_tc_set_wait_budget(v);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(AIR_ERR_CUDA, std::string("setting the wait budget: ") + cudaGetErrorString(e));
+    }
     return AIR_OK;
 }
 

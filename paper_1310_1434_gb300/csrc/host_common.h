@@ -42,4 +42,8 @@ air_status autotune(air_plan *P);
 size_t plan_bytes_estimate(const air_geometry &g);
 air_status apply_filter(const air_plan *P, const SliceDesc &base, const float *src, float *dst,
                         cudaStream_t st);
+// Loads the allocation-free filtered adjoint's static scratch on the current
+// device (CUDA loads a module, and allocates its device arrays, on first
+// use) and records its address; called by plan creation.
+air_status noalloc_prepare();
 }  // namespace air

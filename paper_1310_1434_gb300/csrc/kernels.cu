@@ -1,9 +1,26 @@
 // Kernels of the AIR hot path (sm_103a): per-op kernels over one slice, the
 // task-table kernel over many slices, and the persistent batch kernel.
+#include <atomic>
+
 #include "launch.h"
 #include "tiles.cuh"
 
 namespace air {
+
+// Opts a kernel in to more than 48 KB of dynamic shared memory once per
+// device (the attribute belongs to the device's context): `done` holds one
+// bit per device ordinal below 64; devices beyond that set it every time.
+template <typename Kernel>
+static cudaError_t opt_in_smem(Kernel kernel, std::atomic<unsigned long long> &done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
 
 // ------------------------------------------------------------------------
 // per-op kernels: one block per tile of one slice
@@ -53,13 +70,8 @@ static cudaError_t launch_one(const SliceDesc &s, int arg, cudaStream_t st) {
     const int tiles = tiles_of(s, OP == OP_FRAMELET && arg ? OP_FRAMELET_T : OP);
     if (tiles <= 0) return cudaSuccess;
     const size_t smem = tile_smem(s, OP);
-    static bool attr_done = false;   // opt in to > 48 KB dynamic shared memory once
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_op<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_done = true;
-    }
+    static std::atomic<unsigned long long> attr_done{0};
+    if (cudaError_t e = opt_in_smem(k_op<OP>, attr_done); e != cudaSuccess) return e;
     k_op<OP><<<tiles, AIR_THREADS, smem, st>>>(s, arg);
     return cudaGetLastError();
 }
@@ -156,12 +168,8 @@ k_group(const SliceDesc *__restrict__ slices, const Task *__restrict__ tasks, in
 template <int OP>
 static cudaError_t launch_group_op(const SliceDesc *d_slices, const Task *d_tasks, int ntasks, int total_tiles,
                                    size_t smem, cudaStream_t st) {
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_group<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_done = true;
-    }
+    static std::atomic<unsigned long long> attr_done{0};
+    if (cudaError_t e = opt_in_smem(k_group<OP>, attr_done); e != cudaSuccess) return e;
     k_group<OP><<<total_tiles, AIR_THREADS, smem, st>>>(d_slices, d_tasks, ntasks);
     return cudaGetLastError();
 }
@@ -189,13 +197,8 @@ cudaError_t launch_group(int op, const SliceDesc *d_slices, const Task *d_tasks,
 cudaError_t launch_tasks(const SliceDesc *d_slices, const Task *d_tasks, int ntasks,
                          int total_tiles, size_t smem, cudaStream_t st) {
     if (ntasks <= 0 || total_tiles <= 0) return cudaSuccess;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_tasks, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_done = true;
-    }
+    static std::atomic<unsigned long long> attr_done{0};
+    if (cudaError_t e = opt_in_smem(k_tasks, attr_done); e != cudaSuccess) return e;
     k_tasks<<<total_tiles, AIR_THREADS, smem, st>>>(d_slices, d_tasks, ntasks);
     return cudaGetLastError();
 }
@@ -205,8 +208,15 @@ cudaError_t launch_tasks(const SliceDesc *d_slices, const Task *d_tasks, int nta
 // ------------------------------------------------------------------------
 // Spin budget of one barrier wait: 2^25 polls with a 128 ns back-off, a few
 // seconds, far above any phase; on expiry the block records AIR_ERR_TIMEOUT
-// and every block leaves at its next barrier.
+// and every block leaves at its next barrier.  g_barrier_budget replaces it
+// when >= 0 (air_set_wait_budget; one copy per device).  A block that gives
+// up has no asynchronous copy in flight, so it may leave at once.
 constexpr long long BARRIER_POLLS = 1ll << 25;
+__device__ long long g_barrier_budget = -1;
+
+cudaError_t set_barrier_budget(long long polls) {
+    return cudaMemcpyToSymbol(g_barrier_budget, &polls, sizeof(polls));
+}
 
 __device__ bool grid_barrier(BatchCtl *ctl) {
     __shared__ int ok;
@@ -224,7 +234,8 @@ __device__ bool grid_barrier(BatchCtl *ctl) {
             atomicAdd(&ctl->gen, 1u);
             good = *verr == 0;
         } else {
-            for (long long it = 0; it < BARRIER_POLLS; ++it) {
+            const long long polls = g_barrier_budget < 0 ? BARRIER_POLLS : g_barrier_budget;
+            for (long long it = 0; it < polls; ++it) {
                 if (*vgen != gen) { good = 1; break; }
                 if (*verr != 0) break;
                 __nanosleep(128);
@@ -274,7 +285,8 @@ int persistent_grid(size_t smem) {
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    static std::atomic<unsigned long long> attr_done{0};
+    if (opt_in_smem(k_persistent, attr_done) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent, AIR_THREADS, smem) != cudaSuccess)
         return 0;
     return sms * per;

@@ -40,5 +40,8 @@ cudaError_t launch_persistent(const SliceDesc *d_slices, int nslices, const Phas
                               BatchCtl *d_ctl, int grid, size_t smem, cudaStream_t st);
 // Largest co-resident grid of the persistent kernel for the given smem.
 int persistent_grid(size_t smem);
+// Poll budget of the persistent kernel's grid-barrier wait on the current
+// device (negative: the default).  Synchronous.
+cudaError_t set_barrier_budget(long long polls);
 
 }  // namespace air

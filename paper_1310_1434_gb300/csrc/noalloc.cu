@@ -21,39 +21,67 @@ constexpr size_t NOALLOC_MAX_SAMPLES = size_t(1) << 20;
 // tuned split.
 constexpr size_t NOALLOC_FLOATS = size_t(1) << 22;
 
-// Every GPU that loads this library reserves this array until the process
-// exits.  All calls on a device share it and it keeps the last call's
-// contents; every element a call reads was written earlier by the same call
-// (the filter writes all n_views * n_bins samples, each view part all n * n
-// pixels), so nothing needs clearing.  Calls that overlap on the GPU race on it.
+// The array belongs to this file's module.  CUDA loads a module, and
+// allocates its device arrays, when the module is first used on a device,
+// so plan creation uses it (noalloc_prepare): every device on which a plan
+// has been created holds the array until the process exits, and a later call
+// of the entry point allocates nothing.  All calls on a device share it and
+// it keeps the last call's contents; every element a call reads was written
+// earlier by the same call (the filter writes all n_views * n_bins samples,
+// each view part all n * n pixels), so nothing needs clearing.  Calls that
+// overlap on the GPU race on it.
 static __device__ __align__(256) float g_fbp_scratch[NOALLOC_FLOATS];
 
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 float *g_scratch_ptr[MAX_DEVICES] = {};
 
-// Device address of the scratch on the current device, looked up once per
-// device.  In host code g_fbp_scratch names a host-side stand-in, never a
-// device address, so kernels only ever receive the address returned here.
-air_status scratch_ptr(float **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= MAX_DEVICES) return fail(AIR_ERR_CUDA, "device ordinal out of range");
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_fbp_scratch);
-        if (e != cudaSuccess)
-            return fail(AIR_ERR_CUDA, std::string("cudaGetSymbolAddress of the static scratch: ") +
-                                          cudaGetErrorString(e));
-        g_scratch_ptr[dev] = static_cast<float *>(p);
-    }
+// Looks up the array's device address on the current device and records it.
+// In host code g_fbp_scratch names a host-side stand-in, never a device
+// address, so kernels only ever receive the address recorded here.
+air_status lookup(int dev, float **out) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_fbp_scratch);
+    if (e != cudaSuccess)
+        return fail(AIR_ERR_CUDA, std::string("cudaGetSymbolAddress of the static scratch: ") + cudaGetErrorString(e));
+    g_scratch_ptr[dev] = static_cast<float *>(p);
     *out = g_scratch_ptr[dev];
     return AIR_OK;
 }
 
+air_status current_device(int *dev) {
+    const cudaError_t e = cudaGetDevice(dev);
+    if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (*dev < 0 || *dev >= MAX_DEVICES) return fail(AIR_ERR_CUDA, "device ordinal out of range");
+    return AIR_OK;
+}
+
+// Device address of the scratch on the current device: the one plan creation
+// recorded, or (a device on which no plan was created) looked up now.
+air_status scratch_ptr(float **out) {
+    int dev = 0;
+    air_status st = current_device(&dev);
+    if (st != AIR_OK) return st;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (g_scratch_ptr[dev]) {
+        *out = g_scratch_ptr[dev];
+        return AIR_OK;
+    }
+    return lookup(dev, out);
+}
+
 }  // namespace
+
+// Every plan creation looks the address up again, so a plan created after a
+// cudaDeviceReset (which unloads the module) records the new one.
+air_status air::noalloc_prepare() {
+    int dev = 0;
+    air_status st = current_device(&dev);
+    if (st != AIR_OK) return st;
+    std::lock_guard<std::mutex> lock(g_mu);
+    float *p = nullptr;
+    return lookup(dev, &p);
+}
 
 extern "C" air_status air_filtered_backproject_noalloc(const air_plan *P, const float *Y, float *X,
                                                        air_stream stream) {

@@ -93,9 +93,15 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// Poll budget of the K loop's waits for a stage's operands when >= 0 (see
+// air_set_wait_budget; one copy per device); the waits that drain a CTA's
+// own copies and MMAs before it leaves always keep WAIT_POLLS, so a CTA
+// that gives up never exits with a copy or an MMA in flight.
+__device__ long long g_tc_wait_budget = -1;
+
 // Bounded wait for the completion of the phase with the given parity.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (long long i = 0; i < WAIT_POLLS; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long polls = WAIT_POLLS) {
+    for (long long i = 0; i < polls; ++i) {
         if (mbar_test(bar, parity)) return true;
         if (i > 32) __nanosleep(128);
     }
@@ -206,7 +212,7 @@ k_ramp_gemm(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ C
     uint64_t *empty = full + STAGES;
     uint64_t *done = empty + STAGES;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
-    __shared__ int abort_flag;
+    __shared__ int abort_flag, mma_any;
     const int warp = threadIdx.x >> 5;
     // output parity h: bins 2 i + h, i in [n0, n0 + TN); its input bins are
     // the other parity's, Y columns [a0, a0 + kh) of each piece
@@ -223,6 +229,7 @@ k_ramp_gemm(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ C
         }
         mbar_init(done, 1);
         abort_flag = 0;
+        mma_any = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -242,6 +249,7 @@ k_ramp_gemm(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ C
 
     if (threadIdx.x == 0) {
         // producer + MMA issuer
+        const long long first_polls = g_tc_wait_budget < 0 ? WAIT_POLLS : g_tc_wait_budget;
         bool ok = true;
         int issued = 0;                      // chunks whose loads were issued
         auto load = [&](int kc) {
@@ -262,7 +270,7 @@ k_ramp_gemm(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ C
         int mma_done_through = -1;           // chunks whose MMAs are known complete
         for (int kc = 0; kc < nk && ok; ++kc) {
             const int s = kc % STAGES;
-            if (!mbar_wait(&full[s], (kc / STAGES) & 1)) { ok = false; break; }
+            if (!mbar_wait(&full[s], (kc / STAGES) & 1, first_polls)) { ok = false; break; }
             tc_fence_after();
 #pragma unroll
             for (int q = 0; q < 6; ++q) {
@@ -275,6 +283,7 @@ k_ramp_gemm(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ C
                     umma(tmem + (uint32_t)(acc * TN), da + 2 * ks, db + 2 * ks, first ? 0u : 1u);
                 }
             }
+            mma_any = 1;
             umma_commit(&empty[s]);
             // refill the stage of chunk kc-1 (its MMAs precede kc's) with chunk kc-1+STAGES
             const int prev = kc - 1;
@@ -285,8 +294,9 @@ k_ramp_gemm(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ C
                 load(issued++);
             }
         }
-        // every issued MMA signals `done` when complete
-        umma_commit(done);
+        // every issued MMA signals `done` when complete (a CTA that gave up
+        // before its first MMA has none to wait for)
+        if (mma_any) umma_commit(done);
         if (!ok) {
             abort_flag = 1;
             atomicExch(err, (int)AIR_ERR_TIMEOUT);
@@ -294,9 +304,10 @@ k_ramp_gemm(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ C
             for (int kc = mma_done_through + 1; kc < issued; ++kc) mbar_wait(&full[kc % STAGES], (kc / STAGES) & 1);
         }
     }
-    // everyone waits for the accumulator; the outcome is made block-uniform
-    // because the TMEM loads below are warp-collective
-    const int have = __syncthreads_and(mbar_wait(done, 0) ? 1 : 0);
+    // everyone waits for the producer, then for the accumulator; the outcome
+    // is made block-uniform because the TMEM loads below are warp-collective
+    __syncthreads();
+    const int have = __syncthreads_and(mma_any ? (mbar_wait(done, 0) ? 1 : 0) : 1);
     tc_fence_after();
     if (have && !abort_flag) {
         // lane l of warp w holds row 32 w + l of the tile: it sums the four
@@ -487,7 +498,12 @@ int ramp_tc_status(const air_plan *P) {
     if (!R) return 0;
     int v = 0;
     if (cudaMemcpy(&v, R->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return (int)AIR_ERR_CUDA;
+    if (v != 0 && cudaMemset(R->err, 0, sizeof(int)) != cudaSuccess) return (int)AIR_ERR_CUDA;
     return v;
+}
+
+cudaError_t ramp_tc_set_wait_budget(long long polls) {
+    return cudaMemcpyToSymbol(g_tc_wait_budget, &polls, sizeof(polls));
 }
 
 }  // namespace air

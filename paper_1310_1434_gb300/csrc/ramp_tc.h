@@ -12,6 +12,10 @@ void ramp_tc_destroy(air_plan *P);
 air_status ramp_tc_apply(const air_plan *P, const float *src, float *dst, const CgState *cg,
                          int respect_stop, cudaStream_t st);
 // The plan's tensor-core status word (0, or AIR_ERR_TIMEOUT after a bounded
-// wait gave up); synchronous.
+// wait gave up), cleared once read; synchronous.
 int ramp_tc_status(const air_plan *P);
+// Poll budget of the first pipeline wait of the tensor-core GEMM on the
+// current device (negative: the default); the waits that drain a CTA's own
+// copies and MMAs before it exits keep the default.  Synchronous.
+cudaError_t ramp_tc_set_wait_budget(long long polls);
 }  // namespace air

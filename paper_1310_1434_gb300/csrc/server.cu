@@ -13,6 +13,7 @@
 // state returned to a per-geometry pool, so a warm server allocates nothing.
 // A ring of pinned task tables with one event per entry bounds how many steps
 // the host may run ahead of the GPU.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -68,6 +69,7 @@ struct air_server {
     std::vector<Request *> active;
     std::map<uint64_t, std::unique_ptr<Request>> all;
     std::vector<std::pair<air_geometry, air_plan *>> pool;   // idle plans, reused by geometry
+    std::vector<std::pair<air_geometry, size_t>> plan_bytes; // device bytes of a plan, by geometry, once built
     std::thread worker;
     bool stop = false;
     uint64_t next_id = 1;
@@ -182,10 +184,23 @@ void finish(air_server *S, Request *r, air_status st) {
     S->cv_done.notify_all();
 }
 
-// Admission at a step boundary (called with the lock held).
+// Device bytes of a plan of this geometry: measured once a plan of it has
+// been built, the estimate before.
+size_t request_bytes(const air_server *S, const air_geometry &g) {
+    for (const auto &kv : S->plan_bytes)
+        if (same_geom(kv.first, g)) return kv.second;
+    return plan_bytes_estimate(g);
+}
+
+// Admission at a step boundary (called with the lock held).  A request is
+// charged the bytes of the plan it is given, which are known exactly once
+// the plan exists: a request whose estimate fitted but whose plan does not
+// waits with the plan pooled, and one whose plan alone exceeds the budget
+// fails with AIR_ERR_BUDGET.
 void admit(air_server *S) {
     while (!S->queue.empty() && !S->free_slots.empty()) {
         Request *r = S->queue.front();
+        r->bytes = request_bytes(S, r->geom);
         if (S->used + r->bytes > S->budget) break;       // FIFO: wait for memory
         trim_pool(S, r->bytes);
         air_plan *plan = nullptr;
@@ -194,6 +209,21 @@ void admit(air_server *S) {
             S->queue.pop_front();
             finish(S, r, st);
             continue;
+        }
+        const size_t actual = air_plan_bytes(plan);
+        if (!std::any_of(S->plan_bytes.begin(), S->plan_bytes.end(),
+                         [&](const auto &kv) { return same_geom(kv.first, r->geom); }))
+            S->plan_bytes.push_back({r->geom, actual});
+        if (S->used + actual > S->budget) {
+            r->bytes = actual;
+            if (actual > S->budget) {                     // can never fit
+                air_plan_destroy(plan);
+                S->queue.pop_front();
+                finish(S, r, fail(AIR_ERR_BUDGET, "the request's plan needs more device bytes than the budget"));
+                continue;
+            }
+            put_plan(S, plan);                             // wait for memory with the plan pooled
+            break;
         }
         S->queue.pop_front();
         if (!r->done_ev) {
@@ -215,7 +245,7 @@ void admit(air_server *S) {
             }
         }
         r->plan = plan;
-        r->bytes = air_plan_bytes(plan);
+        r->bytes = actual;
         S->used += r->bytes;
         r->slot = S->free_slots.back();
         S->free_slots.pop_back();

@@ -1,5 +1,6 @@
-"""Batched form: many slices of uneven geometry in one persistent launch give
-the same images as solving each slice alone (pytest -m gpu)."""
+"""Batched form: many slices of uneven geometry, as grouped per-phase launches
+or in one persistent launch, give the same images as solving each slice alone
+and, for one slice of each shape, the FP64 oracle's (pytest -m gpu)."""
 import numpy as np
 import pytest
 
@@ -72,15 +73,25 @@ def test_grouped_batch_mixes_precisions():
         assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b), w.name
 
 
+_ORACLE_64 = {}   # oracle reconstructions of the first slice of each shape, shared by both forms
+
+
+def oracle_64(i, w, Y):
+    import oracle
+    if i not in _ORACLE_64:
+        og = oracle.Geometry(**{k: getattr(w.geom, k) for k in oracle.Geometry.__dataclass_fields__})
+        _ORACLE_64[i] = oracle.solve(og, Y, w.lam, w.mu, w.n_outer, w.n_cg).ravel()
+    return _ORACLE_64[i]
+
+
 @pytest.mark.parametrize("form", ["grouped", "persistent"])
 def test_config2_batch_of_64_uneven_slices(form):
     """The 64-slice batch of uneven geometry (256^2/200 views, 512^2/400,
     512^2/800 and 768^2/800, seeds 100..163), grouped and persistent (whose
     blocks draw tiles from one ticket counter across all 64 slices): every
-    slice equals its single-slice solve, and (grouped) one slice of each shape
-    matches the FP64 oracle (fewer iterations than the benchmark's 30 x 8,
-    which the oracle cannot run 64 times)."""
-    import oracle
+    slice equals its single-slice solve, and in both forms one slice of each
+    shape matches the FP64 oracle (fewer iterations than the benchmark's
+    30 x 8, which the oracle cannot run 64 times)."""
     ws = inputs.batch_workloads(64, n_outer=2, n_cg=2)
     solve = air.air_solve_batch if form == "grouped" else air.air_solve_batch_persistent
     Ys = [torch.as_tensor(f32(inputs.make_case(w)[2]).ravel(), device=DEV) for w in ws]
@@ -95,10 +106,9 @@ def test_config2_batch_of_64_uneven_slices(form):
         a, b = xb.cpu().numpy().astype(np.float64), xs.cpu().numpy().astype(np.float64)
         assert np.all(np.isfinite(a))
         assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b), w.name
-        if i < 4 and form == "grouped":   # one of each shape against the oracle
-            og = oracle.Geometry(**{k: getattr(w.geom, k) for k in oracle.Geometry.__dataclass_fields__})
-            ref = oracle.solve(og, Y.cpu().numpy().astype(np.float64), w.lam, w.mu, w.n_outer, w.n_cg)
-            assert np.linalg.norm(a - ref.ravel()) <= 1e-4 * np.linalg.norm(ref), w.name
+        if i < 4:   # one of each shape against the oracle, in both launch forms
+            ref = oracle_64(i, w, Y.cpu().numpy().astype(np.float64))
+            assert np.linalg.norm(a - ref) <= 1e-4 * np.linalg.norm(ref), (form, w.name)
 
 
 def test_host_buffer_batch_equals_device_batch():

@@ -222,6 +222,24 @@ def test_solve_parity(w):
     assert np.max(np.abs(rg - ro) / np.maximum(ro, 1e-30)) <= 1e-3
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_recursive_cg_restart_over_a_long_solve(prec):
+    """The GPU restarts each outer step's CG from the recursively updated
+    residual r + mu (g_new - g_old); the oracle recomputes rhs - M X.  Equal in
+    exact arithmetic (pinned in FP64 by test_oracle_solver), they could drift
+    apart in FP32 over many outer steps: 100 outer x 5 CG at 128^2 (the
+    128 x 128, 90-view configuration, lambda 0.01, mu 1) still meet the
+    final-image tolerance and the residual history, in FP32 and split BF16."""
+    import dataclasses
+    w = dataclasses.replace(inputs.AIR128, n_outer=100, n_cg=5)
+    g = dataclasses.replace(w.geom, precision=prec)
+    Y = f32(inputs.make_case(w)[2])
+    Xo, ro = oracle.solve(ogeom(g), Y, w.lam, w.mu, w.n_outer, w.n_cg, return_resid=True)
+    Xg, rg = run_solve(g, Y, w.lam, w.mu, w.n_outer, w.n_cg)
+    assert rel(Xg, Xo.ravel()) <= TOL_SOLVE
+    assert np.max(np.abs(rg - ro) / np.maximum(ro, 1e-30)) <= 1e-3
+
+
 def test_solve_edge_cases():
     g = inputs.Geometry(24, 2.0, 16, 40)
     Y = f32(inputs.random_sinogram(16, 40, 3))

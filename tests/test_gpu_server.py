@@ -37,6 +37,12 @@ def alone(w, Y):
     return Xd.cpu().numpy()
 
 
+def oracle_solve(w, Y):
+    import oracle
+    og = oracle.Geometry(**{k: getattr(w.geom, k) for k in oracle.Geometry.__dataclass_fields__})
+    return oracle.solve(og, Y.astype(np.float64), w.lam, w.mu, w.n_outer, w.n_cg).ravel()
+
+
 def test_results_alone_equal_results_in_the_mix():
     ws = mix()
     Ys = [inputs.make_case(w)[2].astype(np.float32).ravel() for w in ws]
@@ -51,8 +57,14 @@ def test_results_alone_equal_results_in_the_mix():
         ref = alone(w, Y)
         assert np.all(np.isfinite(X))
         assert np.linalg.norm(X - ref) <= 1e-4 * np.linalg.norm(ref), w.name
-    for w, X, X1 in zip(ws, res2, res):
+        # every served result of the mix, FP32 and split-BF16, against the
+        # FP64 oracle at the final-image tolerance
+        orc = oracle_solve(w, Y)
+        assert np.linalg.norm(X - orc) <= 1e-4 * np.linalg.norm(orc), w.name
+    for w, Y, X, X1 in zip(ws, Ys, res2, res):
         assert np.linalg.norm(X - X1) <= 1e-6 * np.linalg.norm(X1), w.name
+        orc = oracle_solve(w, Y)
+        assert np.linalg.norm(X - orc) <= 1e-4 * np.linalg.norm(orc), w.name
 
 
 def test_overlap_and_timing_records():

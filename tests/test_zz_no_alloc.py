@@ -66,6 +66,29 @@ def test_noalloc_view_parts(n, V, nb, parts):
     assert np.linalg.norm(a - b) <= TOL * np.linalg.norm(b)
 
 
+def test_noalloc_with_a_split_bf16_plan_uses_the_fp32_filter():
+    # a BF16X3 plan: the allocation-free call applies the FP32 filter, which
+    # differs from the plan's tensor-core filter by rounding only (~2.5e-7)
+    import dataclasses
+    lib = air.load()
+    g = dataclasses.replace(inputs.AIR512_V200.geom, precision=air.PREC_BF16X3)
+    plan = air.Plan(g)
+    ell = inputs.random_phantom(g, 24, 8, 4)
+    Y = inputs.noisy_sinogram(inputs.ellipse_line_integrals(g, ell), 2e4, 24).astype(np.float32)
+    Yd = torch.as_tensor(Y.ravel(), device="cuda")
+    X_ref = torch.empty(g.n * g.n, device="cuda")
+    X_na = torch.full((g.n * g.n,), float("nan"), device="cuda")
+    air.air_filtered_backproject(plan, Yd, X_ref)
+    st = lib.air_filtered_backproject_noalloc(plan.handle, Yd.data_ptr(), X_na.data_ptr(),
+                                              torch.cuda.current_stream().cuda_stream)
+    assert st == air.AIR_OK, air.last_error()
+    torch.cuda.synchronize()
+    a = X_na.cpu().numpy().astype(np.float64)
+    b = X_ref.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(a))
+    assert np.linalg.norm(a - b) <= TOL * np.linalg.norm(b)
+
+
 def test_noalloc_rejects_a_plan_larger_than_its_scratch():
     lib = air.load()
     g = inputs.Geometry(64, 2.0, 1100, 960)     # 1,056,000 samples > 2^20
