@@ -268,7 +268,7 @@ __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile,
             else if (vn < V && mine(en)) fetch(en, vn, (int)(en & 0x3fffu) + lane);
             if (!mixed) {
                 const unsigned kk = (e & VT_NEG) ? BWD_T - 1u - lane : (unsigned)lane;
-#pragma unroll 2
+#pragma unroll 4
                 for (int i = 0; i < cnt; ++i) bwd_ray(stA[i], kk, a);
             } else {
 #pragma unroll 1
