@@ -281,15 +281,36 @@ k_persistent(const SliceDesc *__restrict__ slices, int nslices, const Phase *__r
     }
 }
 
+// Resident blocks per SM of the persistent kernel, and the shared-memory
+// carveout it asks for.  Its shared memory is reserved through every phase
+// (the backprojector's strips), and whatever the carveout leaves is L1, on
+// which the projector phases' gathers depend: four blocks with the carveout
+// sized for them leave about 60 KB of L1 where five leave about 28 KB, and
+// measured 8 % faster on 8-slice 512^2 batches (three blocks lose more
+// parallelism than the L1 gains).
+constexpr int PERSISTENT_BLOCKS = 4;
+
 int persistent_grid(size_t smem) {
-    int dev = 0, sms = 0, per = 0;
+    int dev = 0, sms = 0, per = 0, max_smem = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
+        return 0;
     static std::atomic<unsigned long long> attr_done{0};
     if (opt_in_smem(k_persistent, attr_done) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent, AIR_THREADS, smem) != cudaSuccess)
         return 0;
-    return sms * per;
+    const int blocks = per < PERSISTENT_BLOCKS ? per : PERSISTENT_BLOCKS;
+    if (blocks < 1 || max_smem <= 0) return 0;
+    // the blocks' dynamic and static shared memory plus the 1 KB the
+    // hardware reserves per block, as a percentage of the SM's maximum
+    // (the driver rounds up to a supported carveout)
+    const double need = (double)blocks * ((double)smem + 2048.0);
+    int pct = (int)(100.0 * need / max_smem) + 2;
+    if (pct > 100) pct = 100;
+    if (cudaFuncSetAttribute(k_persistent, cudaFuncAttributePreferredSharedMemoryCarveout, pct) != cudaSuccess)
+        return 0;
+    return sms * blocks;
 }
 
 cudaError_t launch_persistent(const SliceDesc *d_slices, int nslices, const Phase *d_prog,
