@@ -65,26 +65,34 @@ struct CgState {
 };
 
 // One ray in fixed point (32 fractional bits, pixel units, origin at the
-// image corner).  A ray with |ux| >= |uy| (o = 1) is walked column by column:
-// in column k its y-span is [lo(k), lo(k) + Ma] with lo(k) = L0 + k*M; a ray
-// with |uy| > |ux| (o = 0) is walked row by row with x and y exchanged.  The
-// length inside pixel (k, row) is ov * c, ov the integer overlap of the span
-// with [row, row + 1), c = sec/|M|.  Integer arithmetic is exact, so every
-// kernel that evaluates a (ray, pixel) pair gets the same length, bit for bit.
-// The first 16 bytes hold all the backprojector reads: M (0 < |M| < 2^32) is
-// its low word Mlo with the high word given by the sign of cs = +-c.
+// image corner).  A ray with |ux| >= |uy| is walked column by column: in
+// column k its y-span is [lo(k), lo(k) + Ma] with lo(k) = L0 + k*M; a ray
+// with |uy| > |ux| is walked row by row with x and y exchanged.  The length
+// inside pixel (k, row) is ov * c, ov the integer overlap of the span with
+// [row, row + 1), c = sec/|M|.  Integer arithmetic is exact, so every kernel
+// that evaluates a (ray, pixel) pair gets the same length, bit for bit.
+// M (0 < |M| < 2^32) is stored as its low word Mlo, its high word given by
+// the sign of cs = +-c; |M| = Mlo for M > 0 and 2^32 - Mlo for M < 0.  These
+// 16 bytes are all the backprojector reads; the projector also reads the
+// ray's walk word (ray_walk).
 struct __align__(16) RayFx {
     long long L0;      // lower edge of the span in column (row) 0, 2^-32 px
     unsigned Mlo;      // low word of M = slope * 2^32
     float cs;          // c with the sign of M
-    unsigned Ma;       // |M|
-    int kk;            // walk range [kk & 0xffff, kk >> 16)
-    int o;             // 1: walk columns (reads X^T), 0: walk rows (reads X)
-    int pad;
 };
 __host__ __device__ inline long long ray_M(const RayFx &r) {
     return r.cs < 0.f ? (long long)r.Mlo - (1ll << 32) : (long long)r.Mlo;
 }
+__host__ __device__ inline unsigned ray_Ma(const RayFx &r) { return r.cs < 0.f ? 0u - r.Mlo : r.Mlo; }
+// The walk word of a ray: columns (rows) [k0, k1) of the walk in bits 0-15
+// and 16-30, bit 31 set when the ray walks columns (|ux| >= |uy|, reading
+// the transposed image copy).
+__host__ __device__ inline unsigned ray_walk(int k0, int k1, bool cols) {
+    return (unsigned)k0 | ((unsigned)k1 << 16) | (cols ? 0x80000000u : 0u);
+}
+__host__ __device__ inline int walk_k0(unsigned w) { return (int)(w & 0xffffu); }
+__host__ __device__ inline int walk_k1(unsigned w) { return (int)((w >> 16) & 0x7fffu); }
+__host__ __device__ inline int walk_cols(unsigned w) { return (int)(w >> 31); }
 
 // Per (view, backprojector pixel tile): the rays of the view that can meet
 // the tile, [J0, J1), the orientation and slope sign of ray J0, and whether
@@ -106,6 +114,7 @@ struct SliceDesc {
     int filter;          // AIR_FILTER_*
     // tables (plan-owned, read-only)
     const RayFx *ray;    // [V*nb] fixed-point rays
+    const unsigned *walk;  // [V*nb] walk words (ray_walk)
     const unsigned *vt;  // [backprojector pixel tile][V] ray ranges (vt_pack)
     const float *taps;   // [nb] c0 * h[k], k = 0..nb-1 (h even)
     float ramp_diag;     // taps[0] + 2 sum_{odd m < nb} taps[m]

@@ -102,7 +102,7 @@ size_t plan_bytes_estimate(const air_geometry &g) {
     const size_t nn = (size_t)g.n * g.n, rays = (size_t)g.n_views * g.n_bins;
     // the part buffer holds the autotuner's largest split, as plan_build sizes it
     const size_t parts = (size_t)std::min(g.n_views, 2 * choose_bwd_parts(s));
-    size_t b = rays * sizeof(RayFx) + (size_t)g.n_views * tiles_bwd_xy(s) * 4 + (size_t)g.n_bins * 4;
+    size_t b = rays * (sizeof(RayFx) + 4) + (size_t)g.n_views * tiles_bwd_xy(s) * 4 + (size_t)g.n_bins * 4;
     b += nn * 4 * (7 + parts + 18 + 1);          // x r p q rhs0 g g', parts, b b2, xbuf
     b += (size_t)g.n * (g.n + 1) * 8 * 2;        // xp xt (pairs)
     b += (size_t)g.n_views * 8 + (size_t)g.n_bins * 8;   // FBP tables
@@ -127,8 +127,9 @@ long long ceil_div(long long a, long long b) {    // b > 0
 }  // namespace
 
 // The fixed-point form of the line through (px, py) with unit direction
-// (ux, uy), pixel units with the origin at the image corner (see RayFx).
-RayFx air::make_ray_fx(double px, double py, double ux, double uy, int n) {
+// (ux, uy), pixel units with the origin at the image corner (see RayFx), and
+// its walk word.
+RayFx air::make_ray_fx(double px, double py, double ux, double uy, int n, unsigned *walk) {
     const double two32 = 4294967296.0;
     const bool cols = std::fabs(ux) >= std::fabs(uy);       // walk columns
     const double a = cols ? px : py, b = cols ? py : px;    // along / across the walk
@@ -144,20 +145,19 @@ RayFx air::make_ray_fx(double px, double py, double ux, double uy, int n) {
     RayFx r{};
     r.Mlo = (unsigned)(M & 0xffffffffll);
     r.L0 = Y0 + (M < 0 ? M : 0);
-    r.Ma = (unsigned)(M < 0 ? -M : M);
-    const float c = (float)((1.0 / std::fabs(ua)) / (double)r.Ma);
+    const unsigned Ma = (unsigned)(M < 0 ? -M : M);
+    const float c = (float)((1.0 / std::fabs(ua)) / (double)Ma);
     r.cs = M < 0 ? -c : c;
-    r.o = cols ? 1 : 0;
     // walk range: columns k in [0, n) whose span [lo, lo + Ma] meets rows [0, n)
     const long long N2 = (long long)n << 32;
     long long ks, ke;
     if (M > 0) {
-        ks = floor_div(-r.L0 - (long long)r.Ma, M) + 1;     // hi(k) > 0
+        ks = floor_div(-r.L0 - (long long)Ma, M) + 1;       // hi(k) > 0
         ke = ceil_div(N2 - r.L0, M);                        // lo(k) < N2
     } else {
         const long long Mp = -M;
         ks = floor_div(r.L0 - N2, Mp) + 1;                  // lo(k) < N2
-        ke = ceil_div(r.L0 + (long long)r.Ma, Mp);          // hi(k) > 0
+        ke = ceil_div(r.L0 + (long long)Ma, Mp);            // hi(k) > 0
     }
     // clamp to [0, n] before packing: a ray that misses the image can give a
     // start column far outside it (kk holds 16 bits per end)
@@ -165,11 +165,11 @@ RayFx air::make_ray_fx(double px, double py, double ux, double uy, int n) {
     ke = std::min<long long>(std::max<long long>(ke, ks), n);
     auto meets = [&](long long k) {
         const long long lo = r.L0 + k * M;
-        return lo + (long long)r.Ma > 0 && lo < N2;
+        return lo + (long long)Ma > 0 && lo < N2;
     };
     while (ks < ke && !meets(ks)) ++ks;
     while (ke > ks && !meets(ke - 1)) --ke;
-    r.kk = (int)(ks | (ke << 16));
+    *walk = ray_walk((int)ks, (int)ke, cols);
     return r;
 }
 
@@ -291,6 +291,7 @@ air_status autotune(air_plan *P) {
 namespace {
 struct HostTables {
     std::vector<RayFx> ray;
+    std::vector<unsigned> walk;
     std::vector<unsigned> vt;
     std::vector<float> taps, fbw, fbt;
     std::vector<float2> fview;
@@ -303,7 +304,9 @@ air_status build_tables(const air_geometry &g, double dg, int ntxy, HostTables &
     // geometry tables, computed in FP64: per view the source (pixel units,
     // centred) and the central-ray direction; per ray the fixed-point line
     std::vector<RayFx> &hray = T.ray;
+    std::vector<unsigned> &hwalk = T.walk;
     hray.resize(rays);
+    hwalk.resize(rays);
     struct ViewSrc { double x, y, z, w; };   // source (pixel units, centred), central direction
     std::vector<ViewSrc> hsrc(V);
     std::vector<float> &htaps = T.taps;
@@ -321,14 +324,15 @@ air_status build_tables(const air_geometry &g, double dg, int ntxy, HostTables &
             const double su = Sx * ux + Sy * uy;
             // closest point to the image centre, pixel units, origin at the image corner
             const double px = (Sx - su * ux) * inv_dx + 0.5 * n, py = (Sy - su * uy) * inv_dx + 0.5 * n;
-            hray[(size_t)v * nb + j] = make_ray_fx(px, py, ux, uy, n);
+            hray[(size_t)v * nb + j] = make_ray_fx(px, py, ux, uy, n, &hwalk[(size_t)v * nb + j]);
         }
     }
     // the projector walks [k0, k1) without bounds checks (the image copies
     // it reads are padded by one entry per row end): every walked column must
     // lie in the image and its span start in rows [-1, n-1]
-    for (const RayFx &r : hray) {
-        const int k0 = r.kk & 0xffff, k1 = r.kk >> 16;
+    for (size_t i = 0; i < rays; ++i) {
+        const RayFx &r = hray[i];
+        const int k0 = walk_k0(hwalk[i]), k1 = walk_k1(hwalk[i]);
         bool ok = 0 <= k0 && k0 <= k1 && k1 <= n;
         for (int k : {k0, k1 - 1}) {
             if (!ok || k0 == k1) break;
@@ -359,9 +363,11 @@ air_status build_tables(const air_geometry &g, double dg, int ntxy, HostTables &
                     gam[(size_t)iy * (tpr + 1) + ix] = std::atan2(w.z * dys - w.w * dxs, w.z * dxs + w.w * dys);
                 }
             const RayFx *rv = hray.data() + (size_t)v * nb;
+            const unsigned *wv = hwalk.data() + (size_t)v * nb;
             chg[0] = 0;
             for (int j = 1; j < nb; ++j)
-                chg[j] = chg[j - 1] + (rv[j].o != rv[j - 1].o || (rv[j].cs < 0.f) != (rv[j - 1].cs < 0.f));
+                chg[j] = chg[j - 1] +
+                         (walk_cols(wv[j]) != walk_cols(wv[j - 1]) || (rv[j].cs < 0.f) != (rv[j - 1].cs < 0.f));
             for (int ty = 0; ty < tpr; ++ty)
                 for (int tx = 0; tx < tpr; ++tx) {
                     double gmin = 1e30, gmax = -1e30;
@@ -375,7 +381,8 @@ air_status build_tables(const air_geometry &g, double dg, int ntxy, HostTables &
                     const int j0 = (int)std::max(0.0, std::min(f0, (double)nb));
                     const int j1 = (int)std::max(-1.0, std::min(f1, (double)nb - 1));   // inclusive
                     unsigned ent = vt_pack(0, 0, 0, false, false);
-                    if (j1 >= j0) ent = vt_pack(j0, j1 + 1, rv[j0].o, rv[j0].cs < 0.f, chg[j1] != chg[j0]);
+                    if (j1 >= j0)
+                        ent = vt_pack(j0, j1 + 1, walk_cols(wv[j0]), rv[j0].cs < 0.f, chg[j1] != chg[j0]);
                     hvt[(size_t)(ty * tpr + tx) * V + v] = ent;
                 }
         }
@@ -474,6 +481,7 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     float *x, *r, *p, *q, *rhs0, *gg, *gg2, *b, *b2, *z, *zc, *ybuf, *xbuf, *xp, *xt, *bpart;
     const size_t npad = (size_t)n * (n + 1) * 2;   // pair copies of the projector's input (floats)
     RayFx *ray;
+    unsigned *walk;
     unsigned *vt;
     float2 *fview;
     float *fbw, *fbt;
@@ -483,7 +491,8 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     double *partial;
     const size_t npart = (size_t)max_reduce_tiles(s) + 64;
     std::vector<Piece> pieces = {
-        {(void **)&ray, rays * sizeof(RayFx)}, {(void **)&vt, (size_t)V * ntxy * sizeof(unsigned)},
+        {(void **)&ray, rays * sizeof(RayFx)}, {(void **)&walk, rays * sizeof(unsigned)},
+        {(void **)&vt, (size_t)V * ntxy * sizeof(unsigned)},
         {(void **)&xp, npad * 4}, {(void **)&xt, npad * 4}, {(void **)&bpart, (size_t)parts_max * nn * 4},
         {(void **)&taps, (size_t)nb * sizeof(float)}, {(void **)&fview, (size_t)V * sizeof(float2)},
         {(void **)&fbw, (size_t)nb * sizeof(float)}, {(void **)&fbt, (size_t)nb * sizeof(float)},
@@ -512,6 +521,7 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
         return st;
     }
     const std::vector<RayFx> &hray = T->ray;
+    const std::vector<unsigned> &hwalk = T->walk;
     const std::vector<unsigned> &hvt = T->vt;
     const std::vector<float> &htaps = T->taps, &hfbw = T->fbw, &hfbt = T->fbt;
     const std::vector<float2> &hfview = T->fview;
@@ -523,6 +533,7 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
     s.jmid = 0.5f * (nb - 1);
     s.fbp_scale = (float)(g.arc / (double)V / (g.pixel_mm * g.pixel_mm));
     cudaError_t e = cudaMemcpy(ray, hray.data(), rays * sizeof(RayFx), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(walk, hwalk.data(), rays * sizeof(unsigned), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(vt, hvt.data(), hvt.size() * sizeof(unsigned), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(taps, htaps.data(), nb * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(fview, hfview.data(), V * sizeof(float2), cudaMemcpyHostToDevice);
@@ -536,6 +547,7 @@ air_status plan_build(const air_geometry *geom, air_plan *P) {
         return fail(AIR_ERR_CUDA, std::string("plan table upload: ") + cudaGetErrorString(e));
     }
     s.ray = ray;
+    s.walk = walk;
     s.vt = vt;
     s.fview = fview;
     s.fbp_w = fbw;

@@ -36,7 +36,7 @@ air_status check_solve_args(const air_plan *P, const float *Y, float lambda, flo
 SliceDesc solve_desc(const air_plan *P, const float *Y, float lambda, float mu, float *X, double *resid);
 air_status run_program_single(const air_plan *P, const SliceDesc &s, const std::vector<Phase> &prog,
                               cudaStream_t st);
-RayFx make_ray_fx(double px, double py, double ux, double uy, int n);
+RayFx make_ray_fx(double px, double py, double ux, double uy, int n, unsigned *walk);
 int choose_bwd_parts(const SliceDesc &s);
 air_status autotune(air_plan *P);
 size_t plan_bytes_estimate(const air_geometry &g);

@@ -47,12 +47,12 @@ __device__ __forceinline__ void fx_step(long long &lo, const float2 *__restrict_
 // chains), which keeps the ray sum's rounding error within the
 // single-application bound for images up to 1024^2.
 __device__ __forceinline__ float fx_ray(const float2 *__restrict__ XP, const float2 *__restrict__ XTP, int n,
-                                        const RayFx &r) {
-    const int k0 = r.kk & 0xffff, k1 = r.kk >> 16;
+                                        const RayFx &r, unsigned walk) {
+    const int k0 = walk_k0(walk), k1 = walk_k1(walk);
     const int ld = pair_ld(n);
-    const float2 *__restrict__ row = (r.o ? XTP : XP) + (size_t)k0 * ld;   // row k, pair {X[-1], X[0]}
+    const float2 *__restrict__ row = (walk_cols(walk) ? XTP : XP) + (size_t)k0 * ld;   // row k, pair {X[-1], X[0]}
     const long long M = ray_M(r);
-    const unsigned Ma = r.Ma;
+    const unsigned Ma = ray_Ma(r);
     long long lo = r.L0 + (long long)k0 * M;
     float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
     int k = k0;
@@ -78,7 +78,7 @@ __device__ __forceinline__ void tile_fwd(const SliceDesc &s, int arg, int tile) 
     const int idx = v * s.nb + j;
     const RayFx r = s.ray[idx];
     dst[idx] = s.dx * (fabsf(r.cs) * fx_ray(reinterpret_cast<const float2 *>(s.xp),
-                                            reinterpret_cast<const float2 *>(s.xt), s.n, r));
+                                            reinterpret_cast<const float2 *>(s.xt), s.n, r, __ldg(s.walk + idx)));
 }
 
 // xp and xt: the pair copies of src and of its transpose (pair r + 1 of a
@@ -222,10 +222,10 @@ __device__ __forceinline__ void tile_bwd(const SliceDesc &s, int mode, int tile,
     int ro = 0;
     auto fetch = [&](unsigned e, int v, int j) {
         if (j < (int)((e >> 14) & 0x3fffu)) {
-            const RayFx *rp = s.ray + (size_t)v * nb + j;
-            rq = __ldg(reinterpret_cast<const float4 *>(rp));
-            rz = __ldg(Z + (size_t)v * nb + j);
-            if (e & VT_MIXED) ro = rp->o;
+            const size_t ri = (size_t)v * nb + j;
+            rq = __ldg(reinterpret_cast<const float4 *>(s.ray + ri));
+            rz = __ldg(Z + ri);
+            if (e & VT_MIXED) ro = walk_cols(__ldg(s.walk + ri));
         }
     };
     int v = part + S * (warp % BWD_GROUP);
