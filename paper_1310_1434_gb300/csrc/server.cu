@@ -268,6 +268,23 @@ void admit(air_server *S) {
     }
 }
 
+// The end of a step: its ring event, then every active request advances
+// one phase, and one past its last phase copies its image out.
+air_status finish_step(air_server *S, int k) {
+    cudaEventRecord(S->ring_ev[k], S->stream);
+    for (Request *r : S->active) {
+        if (r->state != ACTIVE) continue;
+        if (++r->pc == r->prog.size()) {
+            const size_t img = (size_t)r->geom.n * r->geom.n * 4;
+            cudaError_t e = cudaMemcpyAsync(r->x_pinned, r->plan->xbuf, img, cudaMemcpyDeviceToHost, S->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(r->done_ev, S->stream);
+            if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("server copy-out: ") + cudaGetErrorString(e));
+            r->state = FINISHING;
+        }
+    }
+    return AIR_OK;
+}
+
 // Enqueues one step: every active request advances one phase.
 air_status enqueue_step(air_server *S) {
     const int k = S->ring_pos;
@@ -306,6 +323,25 @@ air_status enqueue_step(air_server *S) {
     if (nt > 0) e = cudaMemcpyAsync(dt, ht, nt * sizeof(Task), cudaMemcpyHostToDevice, S->stream);
     auto it = by_op.find(OP_RAMP_TC);
     const size_t ntc = it != by_op.end() ? it->second.size() : 0;
+    if (launches.size() + ntc == 1) {
+        // one launch (every resident request in the same phase, not a
+        // tensor-core filter): no other launch to overlap with, so it goes
+        // on the server's stream without the fork and join
+        if (e == cudaSuccess && !launches.empty()) {
+            const L &l = launches[0];
+            e = launch_group(l.op, S->d_slices, dt + l.off, l.n, l.tiles, l.smem, S->stream);
+        }
+        if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("server step: ") + cudaGetErrorString(e));
+        air_status st1 = AIR_OK;
+        if (ntc == 1) {
+            Request *r = it->second[0];
+            const SliceDesc &sd = S->h_slices[r->slot];
+            const int arg = r->prog[r->pc].arg;
+            st1 = ramp_tc_apply(r->plan, arg == RSRC_Y ? sd.y : sd.z, sd.zc, sd.cg, arg == RSRC_Z, S->stream);
+        }
+        if (st1 != AIR_OK) return st1;
+        return finish_step(S, k);
+    }
     const int nside = (int)std::min<size_t>(air_server::TC_SIDE, launches.size() + ntc);
     if (e == cudaSuccess) e = cudaEventRecord(S->fork, S->stream);
     for (int q = 0; q < nside && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(S->side[q], S->fork, 0);
@@ -330,19 +366,7 @@ air_status enqueue_step(air_server *S) {
         cudaStreamWaitEvent(S->stream, S->join[k2], 0);
     }
     if (st != AIR_OK) return st;
-    cudaEventRecord(S->ring_ev[k], S->stream);
-    // advance; a request past its last phase copies its image out
-    for (Request *r : S->active) {
-        if (r->state != ACTIVE) continue;
-        if (++r->pc == r->prog.size()) {
-            const size_t img = (size_t)r->geom.n * r->geom.n * 4;
-            e = cudaMemcpyAsync(r->x_pinned, r->plan->xbuf, img, cudaMemcpyDeviceToHost, S->stream);
-            if (e == cudaSuccess) e = cudaEventRecord(r->done_ev, S->stream);
-            if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("server copy-out: ") + cudaGetErrorString(e));
-            r->state = FINISHING;
-        }
-    }
-    return AIR_OK;
+    return finish_step(S, k);
 }
 
 void worker_main(air_server *S) {
