@@ -160,7 +160,7 @@ RayFx air::make_ray_fx(double px, double py, double ux, double uy, int n, unsign
         ke = ceil_div(r.L0 + (long long)Ma, Mp);            // hi(k) > 0
     }
     // clamp to [0, n] before packing: a ray that misses the image can give a
-    // start column far outside it (kk holds 16 bits per end)
+    // start column far outside it (the walk word holds 16 and 15 bits)
     ks = std::min<long long>(std::max<long long>(ks, 0), n);
     ke = std::min<long long>(std::max<long long>(ke, ks), n);
     auto meets = [&](long long k) {
