@@ -26,19 +26,26 @@ namespace air {
 __host__ __device__ inline int pair_ld(int n) { return n + 1; }   // pairs per row of the pair copies
 
 // One column of the walk: the overlaps of the span [lo, lo + Ma] with row r0
-// and (when lo32 + Ma wraps past 2^32) row r0 + 1, times the pixel pair
-// {X[r0], X[r0 + 1]} read with one 8-byte load; without a wrap ov1 = 0.
-__device__ __forceinline__ void fx_step(long long &lo, const float2 *__restrict__ &row, long long M, unsigned Ma,
-                                        int ld, float &a0, float &a1) {
-    const int r0 = (int)(lo >> 32);
-    const unsigned t = (unsigned)lo + Ma;
-    const unsigned ov1 = t < Ma ? t : 0u;      // t < Ma iff the add wrapped
-    const unsigned ov0 = Ma - ov1;
-    const float2 xx = __ldg(row + r0 + 1);
+// and (when the span reaches past the next row boundary) row r0 + 1, times
+// the pixel pair {X[r0], X[r0 + 1]} read with one 8-byte load.  The walk
+// keeps nlo = ~lo: with f = lo mod 2^32 the span's first row takes
+// min(Ma, 2^32 - f) = min(Ma - 1, ~f) + 1 of it (also for f = 0, a span
+// starting on a row boundary) and the next row the rest, 0 when the span
+// ends inside row r0; ~(lo >> 32) = -r0 - 1 turns the pair index off + r0 + 1
+// into one subtraction.  The same integers as the wrap test of the
+// backprojector, with fewer integer instructions on the walk's bound pipe;
+// the image row is a 32-bit element offset into the copy.
+__device__ __forceinline__ void fx_step(long long &nlo, const float2 *__restrict__ copy, unsigned &off, long long M,
+                                        unsigned Ma1, unsigned Ma, int ld, float &a0, float &a1) {
+    const unsigned nf = (unsigned)nlo;                    // ~(lo mod 2^32)
+    const unsigned nr = (unsigned)(nlo >> 32);            // ~r0
+    const unsigned ov0 = min(Ma1, nf) + 1u;
+    const unsigned ov1 = Ma - ov0;
+    const float2 xx = __ldg(copy + (off - nr));           // pair r0 + 1 of row k
     a0 = fmaf(__uint2float_rn(ov0), xx.x, a0);
     a1 = fmaf(__uint2float_rn(ov1), xx.y, a1);
-    lo += M;
-    row += ld;
+    nlo -= M;
+    off += (unsigned)ld;
 }
 
 // Sum over the walk of ov * X (without c), from the pair copies.
@@ -50,17 +57,18 @@ __device__ __forceinline__ float fx_ray(const float2 *__restrict__ XP, const flo
                                         const RayFx &r, unsigned walk) {
     const int k0 = walk_k0(walk), k1 = walk_k1(walk);
     const int ld = pair_ld(n);
-    const float2 *__restrict__ row = (walk_cols(walk) ? XTP : XP) + (size_t)k0 * ld;   // row k, pair {X[-1], X[0]}
+    const float2 *__restrict__ copy = walk_cols(walk) ? XTP : XP;
+    unsigned off = (unsigned)k0 * (unsigned)ld;           // row k0 of the copy, pair {X[-1], X[0]}
     const long long M = ray_M(r);
     const unsigned Ma = ray_Ma(r);
-    long long lo = r.L0 + (long long)k0 * M;
+    long long nlo = ~(r.L0 + (long long)k0 * M);
     float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
     int k = k0;
     for (; k + 1 < k1; k += 2) {
-        fx_step(lo, row, M, Ma, ld, a0, a1);
-        fx_step(lo, row, M, Ma, ld, b0, b1);
+        fx_step(nlo, copy, off, M, Ma - 1u, Ma, ld, a0, a1);
+        fx_step(nlo, copy, off, M, Ma - 1u, Ma, ld, b0, b1);
     }
-    if (k < k1) fx_step(lo, row, M, Ma, ld, a0, a1);
+    if (k < k1) fx_step(nlo, copy, off, M, Ma - 1u, Ma, ld, a0, a1);
     return (a0 + a1) + (b0 + b1);
 }
 
