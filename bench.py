@@ -314,6 +314,32 @@ def oracle_outer_step_seconds(oracle, w):
     return t_rhs, t_outer
 
 
+_ONE_THREAD_SOLVE = """
+import sys, time
+sys.path.insert(0, sys.argv[1])
+import numpy as np, oracle
+from paper_1310_1434_gb300 import inputs
+w = inputs.AIR128
+og = oracle.Geometry(**{k: getattr(w.geom, k) for k in oracle.Geometry.__dataclass_fields__})
+Y = inputs.make_case(w)[2].astype(np.float32).astype(np.float64)
+t = time.perf_counter()
+oracle.solve(og, Y, w.lam, w.mu, w.n_outer, w.n_cg)
+print(oracle.threads(), time.perf_counter() - t)
+"""
+
+
+def oracle_one_thread_seconds():
+    """The oracle's full 128^2 solve on one host thread (OpenMP limited to one
+    thread in a child process), or None if the child fails."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", _ONE_THREAD_SOLVE, ROOT], env=env, capture_output=True,
+                             text=True, timeout=300, check=True).stdout.split()
+        return {"threads": int(out[0]), "air128_v90_full_solve_s": float(out[1])}
+    except (subprocess.SubprocessError, OSError, ValueError, IndexError):
+        return None
+
+
 def cpu_baseline(gpu):
     """The FP64 oracle (as it stands) on this host's cores.  Measured: one
     full split-Bregman solve of the 128^2 configuration (20 x 5), and for
@@ -332,6 +358,9 @@ def cpu_baseline(gpu):
     t = time.perf_counter()
     oracle.solve(og0, Y0, w0.lam, w0.mu, w0.n_outer, w0.n_cg)
     t_c0 = time.perf_counter() - t
+    one = oracle_one_thread_seconds()
+    if one is not None:
+        one["speedup_of_all_threads"] = one["air128_v90_full_solve_s"] / t_c0
     per = {}
     for w in (inputs.AIR512_V800, inputs.AIR512_V200):
         t_rhs, t_outer = oracle_outer_step_seconds(oracle, w)
@@ -374,6 +403,7 @@ def cpu_baseline(gpu):
             "per_config_s": {"air128_v90_full_solve": t_c0,
                              **{k: v["solve_s"] for k, v in per.items()}},
             "per_config_detail": per,
+            "one_thread": one,
             "recorded_full_solves": recorded}, prec
 
 
