@@ -117,22 +117,6 @@ __device__ __forceinline__ const SliceDesc &stage_desc(const SliceDesc *__restri
     return *sd;
 }
 
-__global__ void __launch_bounds__(AIR_THREADS, 5)
-k_tasks(const SliceDesc *__restrict__ slices, const Task *__restrict__ tasks, int ntasks) {
-    extern __shared__ __align__(16) float sm[];
-    __shared__ __align__(16) SliceDesc sd;
-    const int b = blockIdx.x;
-    int lo = 0, hi = ntasks - 1;
-    while (lo < hi) {                 // last task with tile0 <= b
-        const int mid = (lo + hi + 1) >> 1;
-        if (tasks[mid].tile0 <= b) lo = mid;
-        else hi = mid - 1;
-    }
-    const Task t = tasks[lo];
-    int staged = -1;
-    run_tile(stage_desc(slices, t.slice, &sd, &staged), t.op, t.arg, b - t.tile0, sm);
-}
-
 // Grouped form of one op: the tiles of many slices in one launch, the
 // kernel specialised for the op (its own register budget).
 template <int OP>
@@ -192,15 +176,6 @@ cudaError_t launch_group(int op, const SliceDesc *d_slices, const Task *d_tasks,
     case OP_RESTART: return launch_group_op<OP_RESTART>(d_slices, d_tasks, ntasks, total_tiles, smem, st);
     default: return cudaErrorInvalidValue;
     }
-}
-
-cudaError_t launch_tasks(const SliceDesc *d_slices, const Task *d_tasks, int ntasks,
-                         int total_tiles, size_t smem, cudaStream_t st) {
-    if (ntasks <= 0 || total_tiles <= 0) return cudaSuccess;
-    static std::atomic<unsigned long long> attr_done{0};
-    if (cudaError_t e = opt_in_smem(k_tasks, attr_done); e != cudaSuccess) return e;
-    k_tasks<<<total_tiles, AIR_THREADS, smem, st>>>(d_slices, d_tasks, ntasks);
-    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------

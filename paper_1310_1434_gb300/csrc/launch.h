@@ -10,12 +10,6 @@ namespace air {
 // One op over all tiles of one slice.
 cudaError_t launch_op(int op, const SliceDesc &s, int arg, cudaStream_t st);
 
-// One step of many (slice, op) tasks in a single launch; tasks[] and
-// slices[] are device arrays, total_tiles = sum of the tasks' tiles,
-// smem = the largest tile_smem() among them.
-cudaError_t launch_tasks(const SliceDesc *d_slices, const Task *d_tasks, int ntasks,
-                         int total_tiles, size_t smem, cudaStream_t st);
-
 // One op over the tiles of many slices in one launch (tasks all of that op).
 cudaError_t launch_group(int op, const SliceDesc *d_slices, const Task *d_tasks, int ntasks, int total_tiles,
                          size_t smem, cudaStream_t st);
