@@ -4,9 +4,10 @@
 // block of AIR_THREADS threads does one tile of one slice.  The same tile
 // functions back three launch forms:
 //   * per-op kernels over one slice            (air_project, air_solve, ...)
-//   * a task-table kernel over many slices      (serving: mixed ops per step)
+//   * grouped per-op kernels over the tiles of many slices, one launch per
+//     phase (air_solve_batch, captured in a CUDA graph; the server's steps)
 //   * a persistent kernel with a bounded grid barrier between phases
-//     (air_solve_batch)
+//     (air_solve_batch_persistent)
 #pragma once
 
 #include <cstdint>

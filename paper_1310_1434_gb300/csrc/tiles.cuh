@@ -904,7 +904,7 @@ __device__ __forceinline__ void run_shrink(const SliceDesc &s, int arg, int tile
     tile_shrink(s, a, tile, true, nullptr, sm);
 }
 
-// One tile of any op (used by the task-table and persistent kernels).
+// One tile of any op (used by the persistent kernel).
 __device__ __forceinline__ void run_tile(const SliceDesc &s, int op, int arg, int tile, float *sm) {
     switch (op) {
     case OP_FWD: tile_fwd(s, arg, tile); break;
