@@ -778,7 +778,19 @@ def main():
                      "peak_src": f"152 SMs x 4 issue/clk x 32 lanes x {peaks['sm_max_mhz']:.0f} MHz (max SM clock)"
                                  f" / {SEG_INST} instructions per segment",
                      "fwd_frac": nnz / (t_fwd * 1e-3) / 1e9 / seg_peak,
-                     "sm_mhz_under_load": sm_mhz},
+                     "sm_mhz_under_load": sm_mhz,
+                     # the unit that binds both operators: the L1 data pipe
+                     # (one wavefront per SM per clock), the wavefronts per
+                     # launch counted by ncu, the time live
+                     "binding_unit": {
+                         "unit": "L1 data-pipe wavefronts (shared-memory and global loads and stores)",
+                         "bwd_wavefronts_per_launch": BWD_L1_WAVEFRONTS_512_V800,
+                         "fwd_wavefronts_per_launch": FWD_L1_WAVEFRONTS_512_V800,
+                         "peak_per_s": 152 * sm_mhz * 1e6,
+                         "bwd_frac": BWD_L1_WAVEFRONTS_512_V800 / (t_bwd * 1e-3) / (152 * sm_mhz * 1e6),
+                         "fwd_frac": FWD_L1_WAVEFRONTS_512_V800 / (t_fwd * 1e-3) / (152 * sm_mhz * 1e6),
+                         "note": "bwd time includes the part sum k_op<OP_BWD_FIN>; peak at the SM clock "
+                                 "sampled under load"}},
         "cpu_baseline": cpu,
         "precision_vs_fp64_oracle": prec,
     }
@@ -798,6 +810,12 @@ SEG_INST = 8
 # slice, from the committed ncu capture of the current kernel (None when the
 # kernel has changed since).
 BWD_DRAM_BYTES_512_V800 = 11_852_288
+# L1 data-pipe wavefronts of one launch of each operator on the 512^2 /
+# 800-view slice (l1tex__data_pipe_lsu_wavefronts: percent of peak x cycles x
+# 152 SMs) from the committed ncu captures of the current kernels: the
+# backprojector's shared-memory strip updates, the projector's gathers.
+BWD_L1_WAVEFRONTS_512_V800 = 58_059_172
+FWD_L1_WAVEFRONTS_512_V800 = 36_488_677
 
 
 if __name__ == "__main__":
