@@ -179,13 +179,18 @@ constexpr int SHR_T = 16;                      // shrink/framelet output tile
 __host__ __device__ inline int tiles_shr(const SliceDesc &s) {
     return ((s.n + SHR_T - 1) / SHR_T) * ((s.n + SHR_T - 1) / SHR_T);
 }
+// pair-copy transpose tile: 32 x 32 pixels
+__host__ __device__ inline int tiles_tr(const SliceDesc &s) {
+    return ((s.n + 31) / 32) * ((s.n + 31) / 32);
+}
 __host__ __device__ inline int tiles_of(const SliceDesc &s, int op) {
     switch (op) {
     case OP_FWD: return tiles_fwd(s);
     case OP_RAMP: return tiles_ramp(s);
     case OP_BWD: return tiles_bwd(s);
     case OP_CG_A: case OP_CG_B: case OP_ZERO: case OP_BWD_FIN: case OP_AXPY: case OP_RESTART: return tiles_vec(s);
-    case OP_SHRINK: case OP_FRAMELET: case OP_FRAMELET_T: case OP_TRANSPOSE: case OP_PROX: case OP_FBP:
+    case OP_TRANSPOSE: return tiles_tr(s);
+    case OP_SHRINK: case OP_FRAMELET: case OP_FRAMELET_T: case OP_PROX: case OP_FBP:
         return tiles_shr(s);
     default: return 0;
     }
