@@ -1,5 +1,6 @@
-// Kernels of the AIR hot path (sm_103a): per-op kernels over one slice, the
-// task-table kernel over many slices, and the persistent batch kernel.
+// Kernels of the AIR hot path (sm_103a): per-op kernels over one slice,
+// grouped per-op kernels over the tiles of many slices, and the persistent
+// batch kernel.
 #include <atomic>
 
 #include "launch.h"
@@ -98,7 +99,7 @@ cudaError_t launch_op(int op, const SliceDesc &s, int arg, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------------------
-// task-table kernel: block -> (task, tile) by binary search over tile0
+// grouped kernels: block -> (task, tile) by binary search over tile0
 // ------------------------------------------------------------------------
 // The slice descriptor of the current tile is staged in shared memory: the
 // tile functions read its fields inside their loops, which from global
