@@ -28,10 +28,16 @@ namespace {
 // Side streams the tensor-core filters of one phase fork onto during capture
 // (each slice's filter is a small GEMM that fills part of the GPU alone).
 constexpr int TC_SIDE = 8;
+// Independent chains the grouped batch is captured as: slice i runs in chain
+// i mod CHAINS, each chain its phases in order on a stream of its own, so
+// that one chain's launches fill the partly empty last wave of another's.
+constexpr int CHAINS = 2;
 
 struct BatchGraph {
     std::vector<uintptr_t> key;
     cudaStream_t cap = nullptr;     // private stream the graph is captured on
+    cudaStream_t chain[CHAINS] = {};   // chain 0 is cap
+    cudaEvent_t start = nullptr, done[CHAINS] = {};
     cudaStream_t side[TC_SIDE] = {};
     cudaEvent_t fork = nullptr, join[TC_SIDE] = {};
     cudaGraphExec_t exec = nullptr;
@@ -49,6 +55,11 @@ void release(BatchGraph &b) {
     BatchGraph keep;   // the capture streams and events outlive a graph
     keep.cap = b.cap;
     keep.fork = b.fork;
+    keep.start = b.start;
+    for (int c = 0; c < CHAINS; ++c) {
+        keep.chain[c] = b.chain[c];
+        keep.done[c] = b.done[c];
+    }
     for (int i = 0; i < TC_SIDE; ++i) {
         keep.side[i] = b.side[i];
         keep.join[i] = b.join[i];
@@ -59,6 +70,11 @@ void release(BatchGraph &b) {
 cudaError_t make_side_streams(BatchGraph &b) {
     cudaError_t e = cudaSuccess;
     if (!b.fork) e = cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && !b.start) e = cudaEventCreateWithFlags(&b.start, cudaEventDisableTiming);
+    for (int c = 1; c < CHAINS && e == cudaSuccess; ++c) {
+        if (!b.chain[c]) e = cudaStreamCreateWithFlags(&b.chain[c], cudaStreamNonBlocking);
+        if (e == cudaSuccess && !b.done[c]) e = cudaEventCreateWithFlags(&b.done[c], cudaEventDisableTiming);
+    }
     for (int i = 0; i < TC_SIDE && e == cudaSuccess; ++i) {
         if (!b.side[i]) e = cudaStreamCreateWithFlags(&b.side[i], cudaStreamNonBlocking);
         if (e == cudaSuccess && !b.join[i]) e = cudaEventCreateWithFlags(&b.join[i], cudaEventDisableTiming);
@@ -153,31 +169,34 @@ extern "C" air_status air_solve_batch(int n, air_plan *const *plans, const float
     BatchGraph &G = g_grouped;
     if (G.key != B.key || !G.exec) {
         release(G);
-        // phase by phase: one task list per op present in the phase
+        // per chain, phase by phase: one task list per op present in the phase
         struct Launch { int op, off, ntasks, tiles; size_t smem; int slice, arg; };
         std::vector<Task> tasks;
-        std::vector<Launch> launches;
-        for (size_t ph = 0; ph < B.nphases; ++ph) {
-            std::map<int, std::vector<int>> by_op;   // op -> slices
-            for (int i = 0; i < n; ++i)
-                if (ph < B.progs[i].size()) by_op[B.progs[i][ph].op].push_back(i);
-            for (auto &kv : by_op) {
-                const int op = kv.first;
-                if (op == OP_NOP) continue;
-                if (op == OP_RAMP_TC) {   // the tensor-core filter, slice by slice
-                    for (int i : kv.second) launches.push_back({op, 0, 0, 0, 0, i, B.progs[i][ph].arg});
-                    continue;
+        const int nch = std::min(CHAINS, n);
+        std::vector<Launch> launches[CHAINS];
+        for (int c = 0; c < nch; ++c) {
+            for (size_t ph = 0; ph < B.nphases; ++ph) {
+                std::map<int, std::vector<int>> by_op;   // op -> slices of the chain
+                for (int i = c; i < n; i += nch)
+                    if (ph < B.progs[i].size()) by_op[B.progs[i][ph].op].push_back(i);
+                for (auto &kv : by_op) {
+                    const int op = kv.first;
+                    if (op == OP_NOP) continue;
+                    if (op == OP_RAMP_TC) {   // the tensor-core filter, slice by slice
+                        for (int i : kv.second) launches[c].push_back({op, 0, 0, 0, 0, i, B.progs[i][ph].arg});
+                        continue;
+                    }
+                    Launch L{op, (int)tasks.size(), 0, 0, 0, -1, 0};
+                    for (int i : kv.second) {
+                        const int t = tiles_of(B.slices[i], op);
+                        if (t <= 0) continue;
+                        tasks.push_back({i, op, B.progs[i][ph].arg, L.tiles});
+                        L.tiles += t;
+                        L.smem = std::max(L.smem, tile_smem(B.slices[i], op));
+                    }
+                    L.ntasks = (int)tasks.size() - L.off;
+                    if (L.ntasks > 0) launches[c].push_back(L);
                 }
-                Launch L{op, (int)tasks.size(), 0, 0, 0, -1, 0};
-                for (int i : kv.second) {
-                    const int t = tiles_of(B.slices[i], op);
-                    if (t <= 0) continue;
-                    tasks.push_back({i, op, B.progs[i][ph].arg, L.tiles});
-                    L.tiles += t;
-                    L.smem = std::max(L.smem, tile_smem(B.slices[i], op));
-                }
-                L.ntasks = (int)tasks.size() - L.off;
-                if (L.ntasks > 0) launches.push_back(L);
             }
         }
         const size_t b_slices = align_up(n * sizeof(SliceDesc), 256);
@@ -202,36 +221,48 @@ extern "C" air_status air_solve_batch(int n, air_plan *const *plans, const float
             return fail(AIR_ERR_CUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
         }
         const cudaStream_t cs = G.cap;
-        cudaError_t le = cudaSuccess;
+        G.chain[0] = cs;
+        cudaError_t le = cudaEventRecord(G.start, cs);
         std::string tc_msg;
-        for (size_t li = 0; li < launches.size() && le == cudaSuccess && tc_msg.empty(); ++li) {
-            const Launch &L = launches[li];
-            if (L.op != OP_RAMP_TC) {
-                le = launch_group(L.op, d_slices, d_tasks + L.off, L.ntasks, L.tiles, L.smem, cs);
-                continue;
+        for (int c = 0; c < nch && le == cudaSuccess && tc_msg.empty(); ++c) {
+            const cudaStream_t ch = G.chain[c];
+            if (c > 0) le = cudaStreamWaitEvent(ch, G.start, 0);
+            // the chain's share of the side streams
+            const int s0 = c * TC_SIDE / nch, ns = (c + 1) * TC_SIDE / nch - s0;
+            const std::vector<Launch> &ls = launches[c];
+            for (size_t li = 0; li < ls.size() && le == cudaSuccess && tc_msg.empty(); ++li) {
+                const Launch &L = ls[li];
+                if (L.op != OP_RAMP_TC) {
+                    le = launch_group(L.op, d_slices, d_tasks + L.off, L.ntasks, L.tiles, L.smem, ch);
+                    continue;
+                }
+                // a run of tensor-core filters (one phase, one per BF16X3
+                // slice): fork them onto the side streams and join them back
+                size_t end = li;
+                while (end < ls.size() && ls[end].op == OP_RAMP_TC && (end == li || ls[end].slice > ls[end - 1].slice))
+                    ++end;
+                const int nside = (int)std::min<size_t>(ns, end - li);
+                le = cudaEventRecord(G.fork, ch);
+                for (int k = 0; k < nside && le == cudaSuccess; ++k) le = cudaStreamWaitEvent(G.side[s0 + k], G.fork, 0);
+                for (size_t q = li; q < end && le == cudaSuccess && tc_msg.empty(); ++q) {
+                    const Launch &T = ls[q];
+                    const SliceDesc &sd = B.slices[T.slice];
+                    const float *src = T.arg == RSRC_Y ? sd.y : sd.z;
+                    if (ramp_tc_apply(plans[T.slice], src, sd.zc, sd.cg, T.arg == RSRC_Z,
+                                      G.side[s0 + (int)((q - li) % nside)]) != AIR_OK)
+                        tc_msg = air_last_error();
+                }
+                for (int k = 0; k < nside && le == cudaSuccess; ++k) {
+                    le = cudaEventRecord(G.join[s0 + k], G.side[s0 + k]);
+                    if (le == cudaSuccess) le = cudaStreamWaitEvent(ch, G.join[s0 + k], 0);
+                }
+                li = end - 1;
             }
-            // a run of tensor-core filters (one phase, one per BF16X3 slice):
-            // fork them onto the side streams and join them back
-            size_t end = li;
-            while (end < launches.size() && launches[end].op == OP_RAMP_TC &&
-                   (end == li || launches[end].slice > launches[end - 1].slice))
-                ++end;
-            const int nside = (int)std::min<size_t>(TC_SIDE, end - li);
-            le = cudaEventRecord(G.fork, cs);
-            for (int k = 0; k < nside && le == cudaSuccess; ++k) le = cudaStreamWaitEvent(G.side[k], G.fork, 0);
-            for (size_t q = li; q < end && le == cudaSuccess && tc_msg.empty(); ++q) {
-                const Launch &T = launches[q];
-                const SliceDesc &sd = B.slices[T.slice];
-                const float *src = T.arg == RSRC_Y ? sd.y : sd.z;
-                if (ramp_tc_apply(plans[T.slice], src, sd.zc, sd.cg, T.arg == RSRC_Z, G.side[(q - li) % TC_SIDE]) !=
-                    AIR_OK)
-                    tc_msg = air_last_error();
-            }
-            for (int k = 0; k < nside && le == cudaSuccess; ++k) {
-                le = cudaEventRecord(G.join[k], G.side[k]);
-                if (le == cudaSuccess) le = cudaStreamWaitEvent(cs, G.join[k], 0);
-            }
-            li = end - 1;
+        }
+        for (int c = 1; c < nch; ++c) {   // the chains join the capture stream (also after a failure)
+            cudaError_t je = cudaEventRecord(G.done[c], G.chain[c]);
+            if (je == cudaSuccess) je = cudaStreamWaitEvent(cs, G.done[c], 0);
+            if (le == cudaSuccess) le = je;
         }
         if (!tc_msg.empty()) {
             cudaGraph_t g = nullptr;
