@@ -28,10 +28,14 @@ namespace {
 // Side streams the tensor-core filters of one phase fork onto during capture
 // (each slice's filter is a small GEMM that fills part of the GPU alone).
 constexpr int TC_SIDE = 8;
-// Independent chains the grouped batch is captured as: slice i runs in chain
-// i mod CHAINS, each chain its phases in order on a stream of its own, so
-// that one chain's launches fill the partly empty last wave of another's.
+// Independent chains a small grouped batch is captured as: slice i runs in
+// chain i mod CHAINS, each chain its phases in order on a stream of its own,
+// so that one chain's launches fill the partly empty last waves of the
+// other's.  A batch whose backprojector phase takes more than CHAIN_WAVES
+// waves of the device has no such tails to fill, and two chains running
+// large launches side by side are slower: it runs as one chain.
 constexpr int CHAINS = 2;
+constexpr double CHAIN_WAVES = 64.0;
 
 struct BatchGraph {
     std::vector<uintptr_t> key;
@@ -172,7 +176,17 @@ extern "C" air_status air_solve_batch(int n, air_plan *const *plans, const float
         // per chain, phase by phase: one task list per op present in the phase
         struct Launch { int op, off, ntasks, tiles; size_t smem; int slice, arg; };
         std::vector<Task> tasks;
-        const int nch = std::min(CHAINS, n);
+        int nch = std::min(CHAINS, n);
+        {
+            long long bwd_tiles = 0;
+            size_t bwd_smem = 0;
+            for (int i = 0; i < n; ++i) {
+                bwd_tiles += tiles_of(B.slices[i], OP_BWD);
+                bwd_smem = std::max(bwd_smem, tile_smem(B.slices[i], OP_BWD));
+            }
+            const int cap = group_bwd_capacity(bwd_smem);
+            if (cap <= 0 || (double)bwd_tiles > CHAIN_WAVES * cap) nch = 1;
+        }
         std::vector<Launch> launches[CHAINS];
         for (int c = 0; c < nch; ++c) {
             for (size_t ph = 0; ph < B.nphases; ++ph) {

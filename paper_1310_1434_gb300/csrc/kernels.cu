@@ -159,6 +159,19 @@ static cudaError_t launch_group_op(const SliceDesc *d_slices, const Task *d_task
     return cudaGetLastError();
 }
 
+// Blocks of the grouped backprojector that the device holds at once (SMs x
+// blocks per SM at the given shared memory), or 0 on failure.
+int group_bwd_capacity(size_t smem) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    static std::atomic<unsigned long long> attr_done{0};
+    if (opt_in_smem(k_group<OP_BWD>, attr_done) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_group<OP_BWD>, AIR_THREADS, smem) != cudaSuccess)
+        return 0;
+    return sms * per;
+}
+
 cudaError_t launch_group(int op, const SliceDesc *d_slices, const Task *d_tasks, int ntasks, int total_tiles,
                          size_t smem, cudaStream_t st) {
     if (ntasks <= 0 || total_tiles <= 0) return cudaSuccess;

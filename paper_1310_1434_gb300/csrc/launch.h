@@ -10,6 +10,10 @@ namespace air {
 // One op over all tiles of one slice.
 cudaError_t launch_op(int op, const SliceDesc &s, int arg, cudaStream_t st);
 
+// Blocks of the grouped backprojector resident on the current device at
+// once, for the given dynamic shared memory (0 on failure).
+int group_bwd_capacity(size_t smem);
+
 // One op over the tiles of many slices in one launch (tasks all of that op).
 cudaError_t launch_group(int op, const SliceDesc *d_slices, const Task *d_tasks, int ntasks, int total_tiles,
                          size_t smem, cudaStream_t st);
