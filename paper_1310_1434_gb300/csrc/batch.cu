@@ -11,6 +11,7 @@
 // barrier in between, also captured in a graph.  It has one register and
 // shared-memory budget for every op, which costs occupancy on the projector
 // pair; it is kept for callers that want a single launch.
+#include <algorithm>
 #include <climits>
 #include <cstring>
 #include <map>
@@ -28,12 +29,14 @@ namespace {
 // Side streams the tensor-core filters of one phase fork onto during capture
 // (each slice's filter is a small GEMM that fills part of the GPU alone).
 constexpr int TC_SIDE = 8;
-// Independent chains a small grouped batch is captured as: slice i runs in
+// Independent chains a grouped batch may be captured as: slice i runs in
 // chain i mod CHAINS, each chain its phases in order on a stream of its own,
 // so that one chain's launches fill the partly empty last waves of the
-// other's.  A batch whose backprojector phase takes more than CHAIN_WAVES
-// waves of the device has no such tails to fill, and two chains running
-// large launches side by side are slower: it runs as one chain.
+// other's.  Whether that pays depends on the launches (chains of short
+// launches gain, chains of long ones slow each other down), so the first
+// call of a batch times the one-chain and the two-chain graph and keeps the
+// faster.  A batch whose backprojector phase takes more than CHAIN_WAVES
+// waves of the device is not tried in two chains.
 constexpr int CHAINS = 2;
 constexpr double CHAIN_WAVES = 64.0;
 
@@ -128,9 +131,10 @@ air_status prepare(int n, air_plan *const *plans, const float *const *Y, const f
     return AIR_OK;
 }
 
-air_status run_cached(BatchGraph &G, cudaStream_t st) {
-    cudaError_t e = cudaGraphLaunch(G.exec, st);
-    if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("batch graph launch: ") + cudaGetErrorString(e));
+// After a run on st: waits for it, then reads the persistent kernel's barrier
+// status and every tensor-core plan's status.
+air_status finish_run(BatchGraph &G, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
     BatchCtl ctl{};
     if (G.ctl) e = cudaMemcpyAsync(&ctl, G.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -144,6 +148,115 @@ air_status run_cached(BatchGraph &G, cudaStream_t st) {
         if (first == AIR_OK && s != AIR_OK) first = s;
     }
     return first == AIR_OK ? AIR_OK : fail(first, "a bounded wait in a slice's tensor-core filter gave up");
+}
+
+air_status run_cached(BatchGraph &G, cudaStream_t st) {
+    cudaError_t e = cudaGraphLaunch(G.exec, st);
+    if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("batch graph launch: ") + cudaGetErrorString(e));
+    return finish_run(G, st);
+}
+
+// One launch of the grouped form: an op over some slices' tiles, or one
+// slice's tensor-core filter.
+struct Launch { int op, off, ntasks, tiles; size_t smem; int slice, arg; };
+
+// The launch lists of the batch split into nch chains (slice i in chain
+// i mod nch), phase by phase one task list per op present; the tasks are
+// appended to `tasks`.
+void plan_chains(const Batch &B, int n, int nch, std::vector<Task> &tasks, std::vector<Launch> *launches) {
+    for (int c = 0; c < nch; ++c) {
+        for (size_t ph = 0; ph < B.nphases; ++ph) {
+            std::map<int, std::vector<int>> by_op;   // op -> slices of the chain
+            for (int i = c; i < n; i += nch)
+                if (ph < B.progs[i].size()) by_op[B.progs[i][ph].op].push_back(i);
+            for (auto &kv : by_op) {
+                const int op = kv.first;
+                if (op == OP_NOP) continue;
+                if (op == OP_RAMP_TC) {   // the tensor-core filter, slice by slice
+                    for (int i : kv.second) launches[c].push_back({op, 0, 0, 0, 0, i, B.progs[i][ph].arg});
+                    continue;
+                }
+                Launch L{op, (int)tasks.size(), 0, 0, 0, -1, 0};
+                for (int i : kv.second) {
+                    const int t = tiles_of(B.slices[i], op);
+                    if (t <= 0) continue;
+                    tasks.push_back({i, op, B.progs[i][ph].arg, L.tiles});
+                    L.tiles += t;
+                    L.smem = std::max(L.smem, tile_smem(B.slices[i], op));
+                }
+                L.ntasks = (int)tasks.size() - L.off;
+                if (L.ntasks > 0) launches[c].push_back(L);
+            }
+        }
+    }
+}
+
+// Captures the chains' launch lists (each chain on a stream of its own with
+// its share of the filter side streams, all joined at the end) and
+// instantiates them into *exec.
+air_status capture_chains(BatchGraph &G, const Batch &B, air_plan *const *plans, int nch,
+                          const std::vector<Launch> *launches, const SliceDesc *d_slices, const Task *d_tasks,
+                          cudaGraphExec_t *exec) {
+    *exec = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
+    const cudaStream_t cs = G.cap;
+    G.chain[0] = cs;
+    cudaError_t le = cudaEventRecord(G.start, cs);
+    std::string tc_msg;
+    for (int c = 0; c < nch && le == cudaSuccess && tc_msg.empty(); ++c) {
+        const cudaStream_t ch = G.chain[c];
+        if (c > 0) le = cudaStreamWaitEvent(ch, G.start, 0);
+        const int s0 = c * TC_SIDE / nch, ns = (c + 1) * TC_SIDE / nch - s0;   // the chain's side streams
+        const std::vector<Launch> &ls = launches[c];
+        for (size_t li = 0; li < ls.size() && le == cudaSuccess && tc_msg.empty(); ++li) {
+            const Launch &L = ls[li];
+            if (L.op != OP_RAMP_TC) {
+                le = launch_group(L.op, d_slices, d_tasks + L.off, L.ntasks, L.tiles, L.smem, ch);
+                continue;
+            }
+            // a run of tensor-core filters (one phase, one per BF16X3 slice):
+            // fork them onto the side streams and join them back
+            size_t end = li;
+            while (end < ls.size() && ls[end].op == OP_RAMP_TC && (end == li || ls[end].slice > ls[end - 1].slice))
+                ++end;
+            const int nside = (int)std::min<size_t>(ns, end - li);
+            le = cudaEventRecord(G.fork, ch);
+            for (int k = 0; k < nside && le == cudaSuccess; ++k) le = cudaStreamWaitEvent(G.side[s0 + k], G.fork, 0);
+            for (size_t q = li; q < end && le == cudaSuccess && tc_msg.empty(); ++q) {
+                const Launch &T = ls[q];
+                const SliceDesc &sd = B.slices[T.slice];
+                const float *src = T.arg == RSRC_Y ? sd.y : sd.z;
+                if (ramp_tc_apply(plans[T.slice], src, sd.zc, sd.cg, T.arg == RSRC_Z,
+                                  G.side[s0 + (int)((q - li) % nside)]) != AIR_OK)
+                    tc_msg = air_last_error();
+            }
+            for (int k = 0; k < nside && le == cudaSuccess; ++k) {
+                le = cudaEventRecord(G.join[s0 + k], G.side[s0 + k]);
+                if (le == cudaSuccess) le = cudaStreamWaitEvent(ch, G.join[s0 + k], 0);
+            }
+            li = end - 1;
+        }
+    }
+    for (int c = 1; c < nch; ++c) {   // the chains join the capture stream (also after a failure)
+        cudaError_t je = cudaEventRecord(G.done[c], G.chain[c]);
+        if (je == cudaSuccess) je = cudaStreamWaitEvent(cs, G.done[c], 0);
+        if (le == cudaSuccess) le = je;
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cs, &graph);
+    if (le != cudaSuccess) e = le;
+    if (e == cudaSuccess && tc_msg.empty()) e = cudaGraphInstantiate(exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (!tc_msg.empty()) {
+        cudaGetLastError();
+        return fail(AIR_ERR_CUDA, "batch graph build: " + tc_msg);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(AIR_ERR_CUDA, std::string("batch graph build: ") + cudaGetErrorString(e));
+    }
+    return AIR_OK;
 }
 
 air_status end_capture(BatchGraph &G, cudaStream_t cs, cudaError_t launch_err) {
@@ -173,9 +286,8 @@ extern "C" air_status air_solve_batch(int n, air_plan *const *plans, const float
     BatchGraph &G = g_grouped;
     if (G.key != B.key || !G.exec) {
         release(G);
-        // per chain, phase by phase: one task list per op present in the phase
-        struct Launch { int op, off, ntasks, tiles; size_t smem; int slice, arg; };
-        std::vector<Task> tasks;
+        // one chain, and two chains where the batch is small enough for them
+        // to pay (see CHAINS)
         int nch = std::min(CHAINS, n);
         {
             long long bwd_tiles = 0;
@@ -187,32 +299,10 @@ extern "C" air_status air_solve_batch(int n, air_plan *const *plans, const float
             const int cap = group_bwd_capacity(bwd_smem);
             if (cap <= 0 || (double)bwd_tiles > CHAIN_WAVES * cap) nch = 1;
         }
-        std::vector<Launch> launches[CHAINS];
-        for (int c = 0; c < nch; ++c) {
-            for (size_t ph = 0; ph < B.nphases; ++ph) {
-                std::map<int, std::vector<int>> by_op;   // op -> slices of the chain
-                for (int i = c; i < n; i += nch)
-                    if (ph < B.progs[i].size()) by_op[B.progs[i][ph].op].push_back(i);
-                for (auto &kv : by_op) {
-                    const int op = kv.first;
-                    if (op == OP_NOP) continue;
-                    if (op == OP_RAMP_TC) {   // the tensor-core filter, slice by slice
-                        for (int i : kv.second) launches[c].push_back({op, 0, 0, 0, 0, i, B.progs[i][ph].arg});
-                        continue;
-                    }
-                    Launch L{op, (int)tasks.size(), 0, 0, 0, -1, 0};
-                    for (int i : kv.second) {
-                        const int t = tiles_of(B.slices[i], op);
-                        if (t <= 0) continue;
-                        tasks.push_back({i, op, B.progs[i][ph].arg, L.tiles});
-                        L.tiles += t;
-                        L.smem = std::max(L.smem, tile_smem(B.slices[i], op));
-                    }
-                    L.ntasks = (int)tasks.size() - L.off;
-                    if (L.ntasks > 0) launches[c].push_back(L);
-                }
-            }
-        }
+        std::vector<Task> tasks;
+        std::vector<Launch> one[1], many[CHAINS];
+        plan_chains(B, n, 1, tasks, one);
+        if (nch > 1) plan_chains(B, n, nch, tasks, many);
         const size_t b_slices = align_up(n * sizeof(SliceDesc), 256);
         const size_t b_tasks = align_up(std::max<size_t>(tasks.size(), 1) * sizeof(Task), 256);
         if (cudaMalloc(&G.dmem, b_slices + b_tasks) != cudaSuccess) {
@@ -229,67 +319,45 @@ extern "C" air_status air_solve_batch(int n, air_plan *const *plans, const float
         // stream, which cannot be captured); launched on the caller's stream
         if (e == cudaSuccess && !G.cap) e = cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = make_side_streams(G);
-        if (e == cudaSuccess) e = cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) {
             release(G);
             return fail(AIR_ERR_CUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
         }
-        const cudaStream_t cs = G.cap;
-        G.chain[0] = cs;
-        cudaError_t le = cudaEventRecord(G.start, cs);
-        std::string tc_msg;
-        for (int c = 0; c < nch && le == cudaSuccess && tc_msg.empty(); ++c) {
-            const cudaStream_t ch = G.chain[c];
-            if (c > 0) le = cudaStreamWaitEvent(ch, G.start, 0);
-            // the chain's share of the side streams
-            const int s0 = c * TC_SIDE / nch, ns = (c + 1) * TC_SIDE / nch - s0;
-            const std::vector<Launch> &ls = launches[c];
-            for (size_t li = 0; li < ls.size() && le == cudaSuccess && tc_msg.empty(); ++li) {
-                const Launch &L = ls[li];
-                if (L.op != OP_RAMP_TC) {
-                    le = launch_group(L.op, d_slices, d_tasks + L.off, L.ntasks, L.tiles, L.smem, ch);
-                    continue;
-                }
-                // a run of tensor-core filters (one phase, one per BF16X3
-                // slice): fork them onto the side streams and join them back
-                size_t end = li;
-                while (end < ls.size() && ls[end].op == OP_RAMP_TC && (end == li || ls[end].slice > ls[end - 1].slice))
-                    ++end;
-                const int nside = (int)std::min<size_t>(ns, end - li);
-                le = cudaEventRecord(G.fork, ch);
-                for (int k = 0; k < nside && le == cudaSuccess; ++k) le = cudaStreamWaitEvent(G.side[s0 + k], G.fork, 0);
-                for (size_t q = li; q < end && le == cudaSuccess && tc_msg.empty(); ++q) {
-                    const Launch &T = ls[q];
-                    const SliceDesc &sd = B.slices[T.slice];
-                    const float *src = T.arg == RSRC_Y ? sd.y : sd.z;
-                    if (ramp_tc_apply(plans[T.slice], src, sd.zc, sd.cg, T.arg == RSRC_Z,
-                                      G.side[s0 + (int)((q - li) % nside)]) != AIR_OK)
-                        tc_msg = air_last_error();
-                }
-                for (int k = 0; k < nside && le == cudaSuccess; ++k) {
-                    le = cudaEventRecord(G.join[s0 + k], G.side[s0 + k]);
-                    if (le == cudaSuccess) le = cudaStreamWaitEvent(ch, G.join[s0 + k], 0);
-                }
-                li = end - 1;
-            }
-        }
-        for (int c = 1; c < nch; ++c) {   // the chains join the capture stream (also after a failure)
-            cudaError_t je = cudaEventRecord(G.done[c], G.chain[c]);
-            if (je == cudaSuccess) je = cudaStreamWaitEvent(cs, G.done[c], 0);
-            if (le == cudaSuccess) le = je;
-        }
-        if (!tc_msg.empty()) {
-            cudaGraph_t g = nullptr;
-            cudaStreamEndCapture(cs, &g);
-            if (g) cudaGraphDestroy(g);
+        cudaGraphExec_t x1 = nullptr, xn = nullptr;
+        s = capture_chains(G, B, plans, 1, one, d_slices, d_tasks, &x1);
+        if (s == AIR_OK && nch > 1) s = capture_chains(G, B, plans, nch, many, d_slices, d_tasks, &xn);
+        if (s != AIR_OK) {
+            if (x1) cudaGraphExecDestroy(x1);
             release(G);
-            cudaGetLastError();
-            return fail(AIR_ERR_CUDA, "batch graph build: " + tc_msg);
+            return s;
         }
-        if ((s = end_capture(G, cs, le)) != AIR_OK) return s;
         G.key = B.key;
         for (int i = 0; i < n; ++i)
             if (plans[i]->tc) G.tc_plans.push_back(plans[i]);
+        if (!xn) {
+            G.exec = x1;
+        } else {
+            // one timed run of each form on the caller's stream; the faster is
+            // kept.  Both compute the same results, so the second run's output
+            // is this call's.
+            cudaEvent_t ev[3] = {};
+            for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+            if (e == cudaSuccess) e = cudaGraphLaunch(xn, st);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+            if (e == cudaSuccess) e = cudaGraphLaunch(x1, st);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
+            float tn = 0.f, t1 = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&tn, ev[0], ev[1]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ev[1], ev[2]);
+            for (int k = 0; k < 3; ++k)
+                if (ev[k]) cudaEventDestroy(ev[k]);
+            G.exec = (e == cudaSuccess && tn < t1) ? xn : x1;
+            cudaGraphExecDestroy(G.exec == xn ? x1 : xn);
+            if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("batch solve: ") + cudaGetErrorString(e));
+            return finish_run(G, st);
+        }
     }
     return run_cached(G, st);
 }
