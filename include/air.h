@@ -236,12 +236,16 @@ AIR_API air_status air_solve_host(const air_plan *plan, const float *Y_host, flo
 /* Many independent slices of uneven geometry solved together: every slice i
  * is solved as by air_solve(plans[i], Y[i], lambda[i], mu[i], n_outer[i],
  * n_cg[i], X[i]).  The programs advance phase by phase, each phase one
- * grouped launch over the tiles of all slices (FP32 and BF16X3 plans may be
+ * grouped launch over the tiles of its slices (FP32 and BF16X3 plans may be
  * mixed); the launch sequence is captured into a CUDA graph once per batch
- * composition and replayed by later calls with the same arguments.  plans
- * must be distinct (each slice uses its plan's workspace).  Arrays of length
- * n are HOST arrays; Y[i], X[i] are device pointers.  Returns after the
- * batch has finished (synchronises `stream`). */
+ * composition and replayed by later calls with the same arguments.  The
+ * graph runs the slices as one chain of phases or as two independent chains
+ * (slice i in chain i mod 2); the first call of a composition runs both
+ * graphs once, keeps the faster and returns the second run's result, so it
+ * takes about twice as long (batches too large for two chains to pay are
+ * run once).  plans must be distinct (each slice uses its plan's
+ * workspace).  Arrays of length n are HOST arrays; Y[i], X[i] are device
+ * pointers.  Returns after the batch has finished (synchronises `stream`). */
 AIR_API air_status air_solve_batch(int n, air_plan *const *plans, const float *const *Y,
                            const float *lambda, const float *mu, const int *n_outer,
                            const int *n_cg, float *const *X, air_stream stream);
