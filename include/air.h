@@ -241,9 +241,9 @@ AIR_API air_status air_solve_host(const air_plan *plan, const float *Y_host, flo
  * composition and replayed by later calls with the same arguments.  The
  * graph runs the slices as one chain of phases or as two independent chains
  * (slice i in chain i mod 2); the first call of a composition runs both
- * graphs once, keeps the faster and returns the second run's result, so it
- * takes about twice as long (batches too large for two chains to pay are
- * run once).  plans must be distinct (each slice uses its plan's
+ * graphs once (twice each when they are within 3 %), keeps the faster and
+ * returns the last run's result, so it takes two to four times as long
+ * (batches too large for two chains to pay are run once).  plans must be distinct (each slice uses its plan's
  * workspace).  Arrays of length n are HOST arrays; Y[i], X[i] are device
  * pointers.  Returns after the batch has finished (synchronises `stream`). */
 AIR_API air_status air_solve_batch(int n, air_plan *const *plans, const float *const *Y,
