@@ -506,18 +506,13 @@ def main():
     def step():
         air.air_solve_batch(plans, Yd, lam, mu, no, ncg, Xd)
 
-    # kernels per step: one grouped launch per phase of the common program
-    # (5 setup phases, 7 per CG iteration, a shrink per outer step and a CG
-    # restart between outer steps), the filter phases instead as two
-    # tensor-core kernels per slice
-    n_out, n_cgi = ws[0].n_outer, ws[0].n_cg
-    n_phases = 5 + n_out * (7 * n_cgi + 1) + (n_out - 1)
-    n_filter = 1 + n_out * n_cgi
-    launches_per_step = (n_phases - n_filter) + 2 * B * n_filter
-
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
+    # kernels per step, as the library counted them in the graph it chose
+    # (one per grouped phase launch of each chain, two per tensor-core filter
+    # application)
+    graph_chains, launches_per_step = air.air_batch_graph_info()
 
     # ---- timed region: device-resident inputs ----
     clocks = ClockSampler(local)
@@ -547,6 +542,7 @@ def main():
     Yp = [torch.from_numpy(y).pin_memory() for y in Yh]
     Xp = [torch.empty(w.geom.n ** 2, pin_memory=True) for w in ws]
     air.air_solve_batch_host(plans, Yp, lam, mu, no, ncg, Xp)     # captures the host-buffer graph
+    host_chains = air.air_batch_graph_info()[0]
     e2e_ms = []
     for _ in range(args.steps):
         flush.zero_()
@@ -745,8 +741,11 @@ def main():
                    "form": "air_solve_batch: grouped per-phase launches in a CUDA graph, BF16X3 filter",
                    "l2": "flushed between timed steps (256 MB write); working set > L2",
                    "parallelism": f"slices sharded over {world} GPU(s), no collective"},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": [round(t, 2) for t in e2e_ms]},
         "gpu_launches": args.steps * launches_per_step,
+        "batch_graph": {"chains": graph_chains, "kernels_per_step": launches_per_step,
+                        "host_buffer_chains": host_chains},
         "forms_slices_per_s": forms,
         "clocks": clk,
         "plain_gpu": {"path": "air_solve, one slice at a time",

@@ -249,6 +249,14 @@ AIR_API air_status air_solve_host(const air_plan *plan, const float *Y_host, flo
 AIR_API air_status air_solve_batch(int n, air_plan *const *plans, const float *const *Y,
                            const float *lambda, const float *mu, const int *n_outer,
                            const int *n_cg, float *const *X, air_stream stream);
+
+/* Diagnostic description of the grouped batch graph in use (built by the
+ * last air_solve_batch or air_solve_batch_host call that built one; the
+ * paper has no counterpart): its number of chains (1 or 2) and the kernels
+ * one run of it launches (one per grouped phase launch, two per tensor-core
+ * filter application).  Either pointer may be NULL, not both.
+ * AIR_ERR_INVALID_ARG if no batch graph exists yet. */
+AIR_API air_status air_batch_graph_info(int *chains, int64_t *kernels);
 /* air_solve_batch from and to HOST memory: Y_host[i] (n_views*n_bins floats)
  * is copied into plan i's staging buffer, the batch is solved there (the
  * staging buffers are fixed per plan, so repeated calls replay one captured

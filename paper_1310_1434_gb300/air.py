@@ -32,7 +32,7 @@ EXPORTS = ["air_last_error", "air_plan_create", "air_plan_destroy", "air_plan_by
            "air_filter", "air_backproject", "air_filtered_backproject", "air_filtered_backproject_noalloc",
            "air_framelet", "air_shrink",
            "air_solve", "air_solve_l2", "air_solve_fbs", "air_fbp", "air_solve_host",
-           "air_solve_batch", "air_solve_batch_host", "air_solve_batch_persistent",
+           "air_solve_batch", "air_solve_batch_host", "air_solve_batch_persistent", "air_batch_graph_info",
            "air_server_create", "air_server_submit", "air_server_poll", "air_server_wait", "air_server_times",
            "air_server_destroy"]
 
@@ -94,6 +94,7 @@ def load(build_if_missing: bool = False):
         "air_solve_fbs": (i32, [P, P, f32, f32, i32, P, P]),
         "air_solve_batch": (i32, [i32, P, P, P, P, P, P, P, P]),
         "air_solve_batch_persistent": (i32, [i32, P, P, P, P, P, P, P, P]),
+        "air_batch_graph_info": (i32, [ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_int64)]),
         "air_solve_batch_host": (i32, [i32, P, P, P, P, P, P, P, P]),
         "air_server_create": (i32, [ctypes.c_size_t, i32, ctypes.POINTER(P)]),
         "air_server_submit": (i32, [P, g, P, f32, f32, i32, i32, ctypes.POINTER(u64)]),
@@ -304,6 +305,14 @@ def air_solve_batch_host(plans, Ys_host, lams, mus, n_outers, n_cgs, Xs_host, st
 def air_solve_batch_persistent(plans, Ys, lams, mus, n_outers, n_cgs, Xs, stream=None):
     _batch(load().air_solve_batch_persistent, "air_solve_batch_persistent", plans, Ys, lams, mus, n_outers,
            n_cgs, Xs, stream)
+
+
+def air_batch_graph_info():
+    """(chains, kernels per run) of the grouped batch graph in use."""
+    c = ctypes.c_int(0)
+    k = ctypes.c_int64(0)
+    _check(load().air_batch_graph_info(ctypes.byref(c), ctypes.byref(k)), "air_batch_graph_info")
+    return c.value, k.value
 
 
 class Server:

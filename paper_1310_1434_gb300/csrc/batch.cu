@@ -52,6 +52,8 @@ struct BatchGraph {
     char *dmem = nullptr;
     BatchCtl *ctl = nullptr;
     std::vector<const air_plan *> tc_plans;   // plans whose status is checked after a run
+    int chains = 1;                 // of the grouped graph in use
+    long long kernels = 0;          // kernels one run of it launches
 };
 
 std::mutex g_batch_mu;
@@ -197,8 +199,9 @@ void plan_chains(const Batch &B, int n, int nch, std::vector<Task> &tasks, std::
 // instantiates them into *exec.
 air_status capture_chains(BatchGraph &G, const Batch &B, air_plan *const *plans, int nch,
                           const std::vector<Launch> *launches, const SliceDesc *d_slices, const Task *d_tasks,
-                          cudaGraphExec_t *exec) {
+                          cudaGraphExec_t *exec, long long *kernels) {
     *exec = nullptr;
+    *kernels = 0;
     cudaError_t e = cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
     const cudaStream_t cs = G.cap;
@@ -214,6 +217,7 @@ air_status capture_chains(BatchGraph &G, const Batch &B, air_plan *const *plans,
             const Launch &L = ls[li];
             if (L.op != OP_RAMP_TC) {
                 le = launch_group(L.op, d_slices, d_tasks + L.off, L.ntasks, L.tiles, L.smem, ch);
+                *kernels += 1;
                 continue;
             }
             // a run of tensor-core filters (one phase, one per BF16X3 slice):
@@ -231,6 +235,7 @@ air_status capture_chains(BatchGraph &G, const Batch &B, air_plan *const *plans,
                 if (ramp_tc_apply(plans[T.slice], src, sd.zc, sd.cg, T.arg == RSRC_Z,
                                   G.side[s0 + (int)((q - li) % nside)]) != AIR_OK)
                     tc_msg = air_last_error();
+                *kernels += 2;   // the split and the tensor-core product
             }
             for (int k = 0; k < nside && le == cudaSuccess; ++k) {
                 le = cudaEventRecord(G.join[s0 + k], G.side[s0 + k]);
@@ -325,8 +330,9 @@ extern "C" air_status air_solve_batch(int n, air_plan *const *plans, const float
             return fail(AIR_ERR_CUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
         }
         cudaGraphExec_t x1 = nullptr, xn = nullptr;
-        s = capture_chains(G, B, plans, 1, one, d_slices, d_tasks, &x1);
-        if (s == AIR_OK && nch > 1) s = capture_chains(G, B, plans, nch, many, d_slices, d_tasks, &xn);
+        long long k1 = 0, kn = 0;
+        s = capture_chains(G, B, plans, 1, one, d_slices, d_tasks, &x1, &k1);
+        if (s == AIR_OK && nch > 1) s = capture_chains(G, B, plans, nch, many, d_slices, d_tasks, &xn, &kn);
         if (s != AIR_OK) {
             if (x1) cudaGraphExecDestroy(x1);
             release(G);
@@ -335,6 +341,8 @@ extern "C" air_status air_solve_batch(int n, air_plan *const *plans, const float
         G.key = B.key;
         for (int i = 0; i < n; ++i)
             if (plans[i]->tc) G.tc_plans.push_back(plans[i]);
+        G.chains = 1;
+        G.kernels = k1;
         if (!xn) {
             G.exec = x1;
         } else {
@@ -367,6 +375,10 @@ extern "C" air_status air_solve_batch(int n, air_plan *const *plans, const float
                 if (ev[k]) cudaEventDestroy(ev[k]);
             G.exec = (e == cudaSuccess && tn < t1) ? xn : x1;
             cudaGraphExecDestroy(G.exec == xn ? x1 : xn);
+            if (G.exec == xn) {
+                G.chains = nch;
+                G.kernels = kn;
+            }
             if (e != cudaSuccess) return fail(AIR_ERR_CUDA, std::string("batch solve: ") + cudaGetErrorString(e));
             return finish_run(G, st);
         }
@@ -474,4 +486,13 @@ extern "C" air_status air_solve_batch_persistent(int n, air_plan *const *plans, 
         G.key = B.key;
     }
     return run_cached(G, st);
+}
+
+extern "C" air_status air_batch_graph_info(int *chains, int64_t *kernels) {
+    if (!chains && !kernels) return fail(AIR_ERR_INVALID_ARG, "both outputs are NULL");
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    if (!g_grouped.exec) return fail(AIR_ERR_INVALID_ARG, "no batch graph has been built");
+    if (chains) *chains = g_grouped.chains;
+    if (kernels) *kernels = (int64_t)g_grouped.kernels;
+    return AIR_OK;
 }

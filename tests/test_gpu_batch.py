@@ -126,3 +126,27 @@ def test_host_buffer_batch_equals_device_batch():
         air.air_solve_batch_host(plans, Yh, *args, Xh)
         for a, b in zip(Xh, Xd):
             assert torch.equal(a, b.cpu())
+
+
+def test_batch_graph_info_counts_the_launches():
+    # two FP32 slices of one program length: every phase is one grouped launch
+    # per chain (5 set-up phases, 7 per CG step, a shrink per outer step and a
+    # restart between outer steps), whichever chain count the first call chose
+    ws = [inputs._wl("g0", 48, 1.7, 40, 70, 3, 5, 2, 1e5, n_outer=3, n_cg=3),
+          inputs._wl("g1", 64, 1.2, 33, 96, 4, 5, 2, 1e5, n_outer=3, n_cg=3)]
+    Ys = [torch.as_tensor(f32(inputs.make_case(w)[2]).ravel(), device=DEV) for w in ws]
+    plans = [air.Plan(w.geom) for w in ws]
+    Xs = [torch.empty(w.geom.n ** 2, device=DEV) for w in ws]
+    args = ([w.lam for w in ws], [w.mu for w in ws], [w.n_outer for w in ws], [w.n_cg for w in ws])
+    air.air_solve_batch(plans, Ys, *args, Xs)
+    chains, kernels = air.air_batch_graph_info()
+    n_out, n_cg = 3, 3
+    phases = 5 + n_out * (7 * n_cg + 1) + (n_out - 1)
+    assert chains in (1, 2)
+    assert kernels == chains * phases
+    # the replay keeps the chosen graph and its images
+    first = [x.clone() for x in Xs]
+    air.air_solve_batch(plans, Ys, *args, Xs)
+    assert air.air_batch_graph_info() == (chains, kernels)
+    for a, b in zip(first, Xs):
+        assert torch.equal(a, b)
